@@ -1,0 +1,494 @@
+#!/usr/bin/env python
+"""Benchmark: fwd+bwd views/s of the differentiable tile rasterizer on one GB300.
+
+A step is one training view through the whole hot path: gs_project (EWA + SH3
+colour) -> gs_bin_sort -> gs_raster_fwd (Eq. 2) -> gs_l1_loss_grad ->
+gs_raster_bwd -> gs_project_bwd (parameter gradients, with the densification
+statistic fused). Workload: 1.5M Gaussians on 20 surface patches + background,
+SH degree 3, one 1246x826 view per step on a radius-4 orbit, 16x16 tiles (the
+synthetic stand-in for the paper's MipNeRF-360-scale scenes). Inputs are resident
+in HBM; the 354 MB of parameters the step reads exceed the 129 MB L2.
+
+Also reported: the same metric end to end (camera and target image copied from
+pinned host memory, loss read back, every step), the roofline of the dominant
+kernel, per-stage times, the batched mixed-resolution form (12 views in one
+launch per stage, CUDA graph) beside its per-view form, and the FP64 oracle timed
+on the host cores on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 (torchrun), every rank renders its own view of its own replica (the
+path has no exchange step inside a view); value = views of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd views/s at 1.5M Gaussians 1246x826"
+UNIT = "views/s"
+WORKLOAD = "orbit-1.5M-sh3-1246x826"
+# FLOPs per (pixel, list entry) pair, counted from the oracle's operation list:
+# every examined entry costs the falloff (16); a composited entry adds 10 in the
+# forward (transmittance update, weight, 3 colour FMAs) and 46 in the backward.
+FWD_FLOP_EXAM, FWD_FLOP_CONTRIB = 16, 10
+BWD_FLOP_EXAM, BWD_FLOP_CONTRIB = 16, 46
+SM_COUNT_NOMINAL, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--cpu-sample-tiles", type=int, default=48)
+    ap.add_argument("--n", type=int, default=1_500_000)
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+def make_scene(n, rank):
+    from paper_2507_20239_gb300 import synth
+    sc = synth.orbit_scene(1, n=n)
+    if rank:
+        # each rank renders its own orbit view of the same scene
+        cam = sc.cameras[0]
+        az = 2 * math.pi * rank / 8
+        sc.cameras = [synth.orbit_camera(4.0, az + 0.7, 15.0, cam.width, cam.height, cam.fx)]
+    return sc
+
+
+class ViewStep:
+    """Preallocated buffers and the launch sequence of one fwd+bwd training view."""
+
+    def __init__(self, sc, frame, P, capacity):
+        import torch
+        from paper_2507_20239_gb300 import rasterizer as R
+        from paper_2507_20239_gb300.autograd import DensifyStats
+        self.R = R
+        self.sc, self.frame, self.P = sc, frame, P
+        Rn = frame.n_views * sc.n
+        self.proj = R.Projected.empty(Rn, frame.device)
+        self.bins = R.alloc_bins(frame, Rn, capacity)
+        self.image = torch.empty(3 * frame.n_pixels, device=frame.device)
+        self.T = torch.empty(frame.n_pixels, device=frame.device)
+        self.d_image = torch.empty_like(self.image)
+        self.loss = torch.empty(frame.n_views, device=frame.device)
+        self.target = frame.pack_images(sc.targets).contiguous()
+        self.rec = R.RecGrads.zeros(Rn, frame.device)
+        self.pgrads = R.empty_param_grads(P)
+        self.stats = DensifyStats.zeros(sc.n, frame.device)
+
+    def run(self, events=None):
+        R, f = self.R, self.frame
+        ev = events or [None] * 7
+        rec = lambda i: ev[i].record() if ev[i] is not None else None
+        rec(0)
+        R.project(self.P, self.sc.sh_degree, f, out=self.proj)
+        rec(1)
+        R.bin_sort_into(self.proj, f, self.bins)
+        rec(2)
+        R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T)
+        rec(3)
+        R.l1_loss_grad(f, self.image, self.target, d_image=self.d_image, loss=self.loss)
+        rec(4)
+        R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec)
+        rec(5)
+        R.project_bwd(self.P, self.sc.sh_degree, f, self.proj, self.rec, out=self.pgrads,
+                      accum=self.stats.accum, count=self.stats.count)
+        rec(6)
+
+
+STAGES = ["project", "bin_sort", "raster_fwd", "l1_loss_grad", "raster_bwd", "project_bwd"]
+
+
+def measure_capacity(sc, frame, P):
+    from paper_2507_20239_gb300 import rasterizer as R
+    proj = R.project(P, sc.sh_degree, frame)
+    bins = R.bin_sort(proj, frame)
+    M = int(bins.count.item())
+    counts = R.raster_count(proj, bins, frame)
+    c = counts.double().sum(0).cpu().numpy()
+    return M, float(c[0]), float(c[1]), proj
+
+
+def bench_ours(args, rank, local_rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2507_20239_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2507_20239_gb300 import rasterizer as R, _abi
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sc = make_scene(args.n, rank)
+    frame = R.Frame(sc.cameras, device=dev)
+    P = R.to_device_params(sc.params(), dev)
+    M, p_exam, p_contrib, _ = measure_capacity(sc, frame, P)
+    step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        step.run()
+    torch.cuda.synchronize()
+    assert int(step.bins.error.item()) == 0, "duplicate capacity exceeded"
+
+    # ---- device-resident timed region
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = _abi.load().gs_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(args.steps):
+        step.run(events[k])
+    t1.record()
+    torch.cuda.synchronize()
+    launches = (_abi.load().gs_launch_count() - launches0) // args.steps
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    stage_ms = {s: statistics.mean(events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps))
+                for i, s in enumerate(STAGES)}
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end: camera + target H2D from pinned memory, loss D2H, every step
+    tgt_host = step.target.cpu().pin_memory()
+    cam_host = step.frame.cams_dev.cpu().pin_memory()
+    loss_host = torch.empty(frame.n_views, pin_memory=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        step.target.copy_(tgt_host, non_blocking=True)
+        step.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step.frame.cams_dev.copy_(cam_host, non_blocking=True)
+        step.target.copy_(tgt_host, non_blocking=True)
+        step.run()
+        loss_host.copy_(step.loss, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel
+    peaks = load_peaks()
+    fp32_peak = SM_COUNT_NOMINAL * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12     # TFLOP/s
+    dom = max(stage_ms, key=stage_ms.get)
+    flops = {"raster_fwd": FWD_FLOP_EXAM * p_exam + FWD_FLOP_CONTRIB * p_contrib,
+             "raster_bwd": BWD_FLOP_EXAM * p_exam + BWD_FLOP_CONTRIB * p_contrib}
+    n_rec = sc.n * frame.n_views
+    sh_k = sc.sh.shape[1]
+    param_bytes = sc.n * 4 * (3 + 3 + 4 + 1 + 3 * sh_k)
+    bytes_ = {"project": param_bytes + n_rec * 57,
+              "bin_sort": 8 * n_rec * 4 + 8 * M * 2 * 3,
+              "l1_loss_grad": 3 * frame.n_pixels * 4 * 3,
+              "project_bwd": 2 * param_bytes + n_rec * (40 + 57)}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    stages = {}
+    for s in STAGES:
+        d = {"ms": round(stage_ms[s], 4)}
+        if s in flops:
+            a = flops[s] / (stage_ms[s] * 1e-3) / 1e12
+            d.update(bound="alu", achieved_tflops=round(a, 3), frac=round(a / fp32_peak, 4))
+        elif s in bytes_:
+            a = bytes_[s] / (stage_ms[s] * 1e-3) / 1e9
+            d.update(bound="hbm", achieved_gbs=round(a, 1), frac=round(a / hbm_peak, 4))
+        stages[s] = d
+    if dom in flops:
+        ach = flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 1),
+                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure in MEASURED_PEAKS.json)",
+                "traffic": None}
+    else:
+        ach = bytes_.get(dom, 0) / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "traffic": None}
+    traffic = load_traffic(dom)
+    if traffic is not None:
+        roof["traffic"] = traffic
+
+    out = {
+        "metric": METRIC, "value": round(world * 1000.0 / ms, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded surface-patch scene standing in for MipNeRF-360-scale captures)",
+        "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_degree": sc.sh_degree,
+                   "width": sc.cameras[0].width, "height": sc.cameras[0].height, "tile": "16x16",
+                   "views_per_step": frame.n_views, "duplicates_M": M, "pairs_examined": p_exam,
+                   "pairs_composited": p_contrib, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (354 MB parameters read per step)"},
+        "e2e": {"value": round(world * 1000.0 / e2e_ms, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(step.target.numel() * 4 + step.frame.cams_dev.numel()),
+                "d2h_bytes_per_step": int(step.loss.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "stages": stages,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_batched:
+        out["batched"] = bench_batched(args, dev)
+    return out
+
+
+def load_traffic(kernel):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if present."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(kernel)
+    except Exception:
+        return None
+
+
+def bench_batched(args, dev):
+    """12 mixed-resolution views (4 x 312x207, 4 x 623x413, 4 x 1246x826) of a
+    500k-Gaussian scene: one launch per stage, CUDA-graph captured, against the same
+    kernels launched view by view."""
+    import torch
+    from paper_2507_20239_gb300 import rasterizer as R, synth
+    sc = synth.batched_scene(2)
+    P = R.to_device_params(sc.params(), dev)
+    frame = R.Frame(sc.cameras, device=dev)
+    M, _, _, _ = measure_capacity(sc, frame, P)
+    step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step.run()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step.run()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(5, args.steps // 2)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / reps
+    # per-view form: the same kernels, one view per launch
+    singles = []
+    for v, cam in enumerate(sc.cameras):
+        f1 = R.Frame([cam], device=dev)
+        sc1 = synth.Scene(sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh, sc.sh_degree, [cam],
+                          [sc.targets[v]])
+        m1, _, _, _ = measure_capacity(sc1, f1, P)
+        singles.append(ViewStep(sc1, f1, P, int(m1 * 1.25) + 4096))
+    for s in singles:
+        s.run()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for s in singles:
+            s.run()
+    e1.record()
+    torch.cuda.synchronize()
+    per_view_ms = e0.elapsed_time(e1) / reps
+    # same accuracy: the batched images equal the per-view images
+    step.run()
+    torch.cuda.synchronize()
+    same = all(torch.equal(frame.view_image(step.image, v), s.frame.view_image(s.image, 0))
+               for v, s in enumerate(singles))
+    nv = len(sc.cameras)
+    return {"workload": "batched-500k-sh3-12views-mixed-res", "views_per_launch": nv,
+            "batched_views_per_s": round(nv * 1000.0 / batched_ms, 2),
+            "per_view_views_per_s": round(nv * 1000.0 / per_view_ms, 2),
+            "batched_ms": round(batched_ms, 4), "per_view_ms": round(per_view_ms, 4),
+            "images_identical": bool(same), "graph": True}
+
+
+# ----------------------------------------------------------------------------------------
+def oracle_view_seconds(sc, n_tiles_sample, seed=0):
+    """Time the FP64 oracle on a bounded sample of one training view and scale it to
+    a whole view: projection of all Gaussians, tile binning, compositing + backward of
+    n_tiles_sample tiles (scaled by tiles), projection VJP of a Gaussian sample
+    (scaled by count)."""
+    import torch
+    from oracle import project as oproj, raster as oras, pipeline as opipe
+    cam = sc.cameras[0]
+    t0 = time.perf_counter()
+    pr = oproj.project_np(sc.params(), sc.sh_degree, cam)
+    t_proj = time.perf_counter() - t0
+    gx, gy = pr["grid"]
+    t0 = time.perf_counter()
+    lists = oras.tile_lists(pr["rect"], pr["depth"].astype(np.float32), gx, gy)
+    t_bin = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    busy = [t for t, l in lists.items() if len(l)]
+    tiles = sorted(rng.choice(busy, min(n_tiles_sample, len(busy)), replace=False).tolist())
+    d_image = rng.normal(0, 1, (3, cam.height, cam.width))
+    t0 = time.perf_counter()
+    oras.raster_vjp(pr["mean2d"], pr["conic"], pr["opacity"], pr["rgb"], lists, cam.width, cam.height, d_image,
+                    tiles=tiles)
+    t_tiles = time.perf_counter() - t0
+    n_s = min(sc.n, 100_000)
+    sub = {k: v[:n_s] for k, v in sc.params().items()}
+    g = dict(d_mean2d=rng.normal(size=(n_s, 2)), d_conic=rng.normal(size=(n_s, 3)), d_opacity=rng.normal(size=n_s),
+             d_rgb=rng.normal(size=(n_s, 3)))
+    t0 = time.perf_counter()
+    opipe.project_vjp(sub, sc.sh_degree, [cam], [g])
+    t_vjp = time.perf_counter() - t0
+    total = t_proj + t_bin + t_tiles * gx * gy / len(tiles) + t_vjp * sc.n / n_s
+    spent = t_proj + t_bin + t_tiles + t_vjp
+    sample = (f"1 view of {WORKLOAD}: projection of all {sc.n} Gaussians, binning, Eq. 2 forward+backward on "
+              f"{len(tiles)} of {gx * gy} tiles (x{gx * gy / len(tiles):.1f}), projection VJP on {n_s} Gaussians "
+              f"(x{sc.n / n_s:.1f}); {spent:.1f} s of CPU time")
+    return total, spent, sample, torch.get_num_threads()
+
+
+def cpu_baseline(sc, n_tiles):
+    total, spent, sample, cores = oracle_view_seconds(sc, n_tiles)
+    return {"value": round(1.0 / total, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def bench_reference(args, rank, world):
+    """The FP64 oracle as the reference arm, on the host cores."""
+    if rank != 0:
+        return None
+    sc = make_scene(args.n, 0)
+    steps = max(1, min(args.steps, 3))
+    tiles = max(4, args.cpu_sample_tiles // 2)
+    for _ in range(min(args.warmup, 1)):
+        oracle_view_seconds(sc, 4)
+    times, spent_all, sample, cores = [], 0.0, "", 1
+    for k in range(steps):
+        total, spent, sample, cores = oracle_view_seconds(sc, tiles, seed=k)
+        times.append(total)
+        spent_all += spent
+    ms = 1000.0 * statistics.mean(times)
+    v = round(1000.0 / ms, 6)
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": min(args.warmup, 1),
+            "ms_per_step": round(ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "width": sc.cameras[0].width,
+                       "height": sc.cameras[0].height, "tile": "16x16"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_info()
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        out = bench_reference(args, rank, world)
+        print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = bench_ours(args, rank, local_rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(make_scene(args.n, 0), args.cpu_sample_tiles)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

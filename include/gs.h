@@ -1,0 +1,309 @@
+/*
+ * libgs -- GB300 (sm_103a) differentiable tile rasterizer for 3D Gaussian splatting,
+ * with the densification bookkeeping of the paper's training loop.
+ *
+ * Paper: "Decomposing Densification in Gaussian Splatting for Faster 3D Scene
+ * Reconstruction" (arXiv 2507.20239). The rasterizer computes the paper's Eq. 1 /
+ * EWA projection / Eq. 2 (Sec. "Preliminary"); densification follows the
+ * split/clone rule (Sec. "Preliminary", last paragraph), global-to-local gating
+ * (Sec. "Global-to-local framework") and adaptive opacity pruning (Sec. "Adaptive
+ * Opacity Pruning").
+ *
+ * Conventions for every entry point:
+ *  - Every pointer named *_dev or documented as "device" is CUDA device memory
+ *    owned by the caller. The library never allocates, frees or synchronises:
+ *    each call enqueues kernels on `stream` and returns. Calls on one stream may
+ *    be captured into a CUDA graph.
+ *  - Scratch memory is the caller's `ws` buffer of at least the size returned by
+ *    the matching *_workspace_size function, 256-byte aligned.
+ *  - Argument errors are detected on the host before anything is enqueued and
+ *    returned as GS_ERR_INVALID_ARG. Launch failures return GS_ERR_CUDA.
+ *    Conditions only the device can see (duplicate or output capacity exceeded)
+ *    are OR-ed as GS_ERR_* bits into the caller's device word `d_error`, which
+ *    the caller reads after the stream has been synchronised (outside any graph).
+ *  - Floating point data are IEEE fp32, contiguous, row-major; all base pointers
+ *    are 16-byte aligned. Records of view v and Gaussian g have index r = v*n + g.
+ *  - No entry point traps or spins without a bound.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,
+  GS_ERR_CAPACITY = 2,     /* a device-side count exceeded a caller capacity     */
+  GS_ERR_CUDA = 3,         /* a CUDA launch or runtime call failed               */
+  GS_ERR_TIMEOUT = 4,      /* a bounded device wait ran out (reserved)           */
+  GS_ERR_UNSUPPORTED = 5   /* valid request this build does not implement        */
+} gs_status_t;
+
+typedef void *gs_stream_t; /* a cudaStream_t; NULL = the legacy default stream */
+
+/* One pinhole view. World->camera rotation R (row-major) and translation t, OpenCV
+ * axes (x right, y down, z forward); pixel (i, j) is sampled at (i + 0.5, j + 0.5).
+ * The last five fields are layout, written by gs_frame_init. */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_plane;        /* records with camera-space z <= near_plane are culled */
+  int32_t grid_x, grid_y;  /* tiles per row / column                              */
+  int32_t tile_offset;     /* first global tile index of this view                */
+  int64_t pixel_offset;    /* first pixel of this view in planar batch buffers    */
+} gs_camera_t;
+
+/* A batch of views rendered together. cams_dev is a device copy of the cameras
+ * (after gs_frame_init). Tiles of all views form one global index space
+ * [0, n_tiles); images are stored view after view, each planar [3][H][W] starting
+ * at float offset 3 * pixel_offset. */
+typedef struct {
+  const gs_camera_t *cams_dev;
+  int32_t n_views;
+  int32_t tile_w, tile_h;  /* 16x16 (default), 8x8 or 16x32 (w x h); see gs_tile_supported */
+  int32_t n_tiles;
+  int64_t n_pixels;
+  int32_t max_width, max_height;
+} gs_frame_t;
+
+/* Gaussian parameters, device SoA (Eq. 1: position, scale, rotation, opacity, SH):
+ * means [n][3]; log_scales [n][3] (scale = exp); quats [n][4] as (w, x, y, z), any
+ * norm > 0 (normalised inside); opacity_logits [n] (opacity = sigmoid);
+ * sh [n][sh_stride][3] real SH coefficients, index k = l*l + l + m, Condon-Shortley
+ * phase, colour = sum_k sh_k Y_k(dir) + 0.5 clamped at 0, dir = unit vector from
+ * the camera centre to the mean. sh_degree in 0..3, sh_stride >= (sh_degree+1)^2. */
+typedef struct {
+  const float *means;
+  const float *log_scales;
+  const float *quats;
+  const float *opacity_logits;
+  const float *sh;
+  int64_t n;
+  int32_t sh_degree;
+  int32_t sh_stride;
+} gs_params_t;
+
+/* Projected records (device, caller-allocated, n_records = n_views * n rows each).
+ * mean2d [R][2] pixels; conic_opacity [R][4] = (A, B, C, opacity) with the Gaussian
+ * power P = -1/2 (A dx^2 + C dy^2) - B dx dy, (A B; B C) = (Sigma' + 0.3 I)^-1;
+ * rgb [R][4] = (r, g, b, 0); depth [R] camera-space z; radius [R] = ceil(3 sqrt(
+ * lambda_max)), 0 = culled; rect [R][4] tile rectangle x0, y0, x1, y1 (exclusive);
+ * clamped [R] bit c set when colour channel c was clamped at 0. */
+typedef struct {
+  float *mean2d;
+  float *conic_opacity;
+  float *rgb;
+  float *depth;
+  int32_t *radius;
+  uint16_t *rect;
+  uint8_t *clamped;
+  int64_t n_records;
+} gs_proj_t;
+
+/* Per-tile depth-sorted lists (device). vals [capacity]: record indices ordered by
+ * (global tile, FP32 depth bits, record index); keys [capacity] optional (may be
+ * NULL): tile << 32 | depth bits of the same entries; ranges [n_tiles][2]: start,
+ * end of each tile in vals (start == end for an empty tile); d_count [1] (int64):
+ * the number of entries M, written by gs_bin_sort. */
+typedef struct {
+  uint32_t *vals;
+  uint64_t *keys;
+  uint32_t *ranges;
+  int64_t *d_count;
+  int64_t capacity;
+} gs_bins_t;
+
+typedef struct {
+  float bg[3];             /* background colour (default black)                   */
+  int32_t store_stop;      /* write the per-pixel stop index in gs_raster_fwd     */
+} gs_raster_cfg_t;
+
+/* Gradients of the loss w.r.t. the projected records (device, [R] rows, same row
+ * layout as gs_proj_t): d_mean2d [R][2], d_conic_opacity [R][4], d_rgb [R][4].
+ * gs_raster_bwd OVERWRITES them (it clears them, then accumulates). */
+typedef struct {
+  float *d_mean2d;
+  float *d_conic_opacity;
+  float *d_rgb;
+} gs_rec_grads_t;
+
+/* Gradients w.r.t. the Gaussian parameters (device, same shapes as gs_params_t;
+ * d_sh uses the params' sh_stride). gs_project_bwd OVERWRITES them. */
+typedef struct {
+  float *d_means;
+  float *d_log_scales;
+  float *d_quats;
+  float *d_opacity_logits;
+  float *d_sh;
+} gs_param_grads_t;
+
+/* ---------------------------------------------------------------------- host helpers */
+
+const char *gs_status_str(gs_status_t s);
+const char *gs_version(void);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded (a host-side
+ * counter; graph replays of captured launches are not counted again). */
+uint64_t gs_launch_count(void);
+
+/* Nonzero when the tile shape tile_w x tile_h has compiled kernels. */
+int32_t gs_tile_supported(int32_t tile_w, int32_t tile_h);
+
+/* Fill the layout fields of cams_host[0..n_views) and the frame's counts (tile grid
+ * per view, global tile and pixel offsets). Host memory only; cams_dev is left for
+ * the caller to set after copying cams_host to the device. */
+gs_status_t gs_frame_init(gs_camera_t *cams_host, int32_t n_views, int32_t tile_w,
+                          int32_t tile_h, gs_frame_t *frame);
+
+/* Bytes of scratch gs_bin_sort needs for n_records records and dup_capacity
+ * duplicates on this frame. */
+size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const gs_frame_t *frame);
+
+/* ---------------------------------------------------------------------- hot path */
+
+/* EWA projection + SH colour of every (view, Gaussian) record -- Eq. 1, the paper's
+ * Sigma' = J W Sigma W^T J^T, and the SH-evaluated colour c_i of Eq. 2.
+ * Readings: near-plane cull; J at the mean with t_x/t_z, t_y/t_z clamped to
+ * +-1.3 (W/2)/f; Sigma' + 0.3 I; cull det <= 0; radius = ceil(3 sqrt(m +
+ * sqrt(max(0.1, m^2 - det)))); cull when the tile rectangle is empty.
+ * Culled records get radius 0 and an empty rect; their other fields are zero. */
+gs_status_t gs_project(const gs_params_t *params, const gs_frame_t *frame, gs_proj_t *out,
+                       gs_stream_t stream);
+
+/* Tile binning and depth sort ("tile-based", "depth-sorted"; Sec. "Preliminary").
+ * Every visible record is duplicated into each tile of its rectangle; duplicates
+ * are ordered by (global tile, FP32 depth bits, record index) and the per-tile
+ * ranges written. Device-side: if M > bins->capacity, GS_ERR_CAPACITY is OR-ed into
+ * *d_error, *bins->d_count receives the required M and vals/ranges are left
+ * empty (every range [0, 0)). */
+gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *frame, gs_bins_t *bins,
+                        void *ws, size_t ws_bytes, int32_t *d_error, gs_stream_t stream);
+
+/* Front-to-back alpha compositing, Eq. 2, per pixel over its tile's list:
+ * sigma = min(0.99, o exp(P)), entries with P > 0 or sigma < 1/255 skipped, the walk
+ * stops before the entry that would make T < 1e-4; out = C + T bg.
+ * image [3 * n_pixels] planar per view; T_final [n_pixels]; stop [n_pixels] (one
+ * past the last contributing list position) written when cfg->store_stop and stop
+ * is not NULL. */
+gs_status_t gs_raster_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                          const gs_raster_cfg_t *cfg, float *image, float *T_final,
+                          uint32_t *stop, gs_stream_t stream);
+
+/* Work count of Eq. 2 (a measurement aid, not part of training): runs the forward's
+ * per-pixel walk and writes, per pixel, counts[2p] = list entries examined up to and
+ * including the one that triggers the transmittance cut-off (or the whole list) and
+ * counts[2p+1] = entries composited. counts [n_pixels][2], 8-byte aligned. */
+gs_status_t gs_raster_count(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                            uint32_t *counts, gs_stream_t stream);
+
+/* L1 photometric loss (the L1 term of Eq. 3) per view, mean over 3*H*W:
+ * d_image = sign(image - target) / (3 H W) (0 at equality); loss_dev [n_views]
+ * receives each view's loss (overwritten). */
+gs_status_t gs_l1_loss_grad(const gs_frame_t *frame, const float *image, const float *target,
+                            float *d_image, float *loss_dev, gs_stream_t stream);
+
+/* Gradient of Eq. 2 w.r.t. every record's mean2d, conic, opacity and colour, given
+ * dL/d image. Re-walks each pixel's list front to back with the forward's exact
+ * FP32 recurrence (so the stop position is recomputed, not stored) and uses
+ * dL/dsigma_i = T_i <c_i, g> - (<out, g> - sum_{j<=i} <c_j, g> sigma_j T_j) / (1 - sigma_i),
+ * out being the forward's image; zero through the 0.99 clamp. Per-pixel terms are
+ * summed per Gaussian in registers, across the warp and the CTA, then added once
+ * per (tile, record) into grads (see gs_rec_grads_t). */
+gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                          const gs_raster_cfg_t *cfg, const float *image, const float *d_image,
+                          gs_rec_grads_t *grads, gs_stream_t stream);
+
+/* Vector-Jacobian product of gs_project: record gradients -> parameter gradients,
+ * summed over views (chain rule through the conic inverse, Sigma' = J W Sigma W^T J^T,
+ * Sigma = R S S^T R^T, the quaternion normalisation, exp scales, the J clamp, the
+ * pinhole mean, SH colour with its clamp and direction, and the opacity sigmoid).
+ * If densify_accum / densify_count are not NULL the densification statistic of
+ * gs_densify_accum is fused in. */
+gs_status_t gs_project_bwd(const gs_params_t *params, const gs_frame_t *frame,
+                           const gs_proj_t *proj, const gs_rec_grads_t *rec_grads,
+                           gs_param_grads_t *out, float *densify_accum,
+                           int32_t *densify_count, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------- densification */
+
+typedef enum {
+  GS_DENSIFY_ADAPTIVE = 0,   /* split if large, clone otherwise (the standard rule)      */
+  GS_DENSIFY_SPLIT_ONLY = 1, /* global phase of global-to-local: clone disabled          */
+  GS_DENSIFY_ALL_SPLIT = 2,  /* every selected Gaussian splits (split-only analysis)     */
+  GS_DENSIFY_ALL_CLONE = 3   /* every selected Gaussian clones (clone-only analysis)     */
+} gs_densify_mode_t;
+
+typedef struct {
+  int32_t mode;              /* gs_densify_mode_t                                         */
+  float grad_threshold;      /* 2e-4: select when accum/count > this                      */
+  float log_scale_threshold; /* split when max log-scale > this (FP32 of log(0.01 extent)) */
+  int32_t prune_adaptive;    /* 0: fixed logit threshold; 1: adaptive order statistic     */
+  float prune_logit;         /* fixed: prune when logit < prune_logit                     */
+  float prune_upper_logit;   /* adaptive: FP32 logit(tau_u)                               */
+  double prune_ratio;        /* adaptive: p, k = min(floor(N' p), N' - 1)                 */
+  uint64_t seed;             /* Philox key for split children                             */
+  uint32_t event;            /* densification event counter (Philox counter word 2)      */
+} gs_densify_cfg_t;
+
+/* View-space gradient statistic (Sec. "Preliminary": norm of the average position
+ * gradient): for each view v in order and Gaussian g with radius > 0,
+ * accum[g] += sqrt(gx^2 + gy^2), (gx, gy) = d_mean2d[v*n+g] * (W_v/2, H_v/2),
+ * count[g] += 1 (FP32, one rounding per operation). */
+gs_status_t gs_densify_accum(const float *d_mean2d, const int32_t *radius, const gs_frame_t *frame,
+                             int64_t n, float *accum, int32_t *count, gs_stream_t stream);
+
+size_t gs_densify_workspace_size(int64_t n);
+
+/* Split/clone masks and the pruning threshold. split[g], clone[g] in {0,1};
+ * *d_tau_logit receives the prune threshold in logit space (fixed, or
+ * min(k-th smallest logit of the post-densification multiset, prune_upper_logit)
+ * for adaptive pruning, Sec. "Adaptive Opacity Pruning"); *d_new_n receives the
+ * Gaussian count after densification and pruning. */
+gs_status_t gs_densify_select(const gs_densify_cfg_t *cfg, const float *log_scales,
+                              const float *opacity_logits, const float *accum,
+                              const int32_t *count, int64_t n, uint8_t *split, uint8_t *clone,
+                              float *d_tau_logit, int64_t *d_new_n, void *ws, size_t ws_bytes,
+                              gs_stream_t stream);
+
+/* One extra per-Gaussian float array carried through compaction (e.g. an optimiser
+ * moment): survivors keep their row, new rows are zero. */
+typedef struct {
+  const float *src;
+  float *dst;
+  int32_t width;           /* floats per Gaussian */
+} gs_extra_array_t;
+
+/* Output parameter arrays of gs_densify_apply (device, capacity rows each). */
+typedef struct {
+  float *means;
+  float *log_scales;
+  float *quats;
+  float *opacity_logits;
+  float *sh;
+} gs_params_out_t;
+
+/* Densify + prune + compaction. Output rows: survivors (kept, not split) in
+ * original order, then clones in parent order, then split children in parent order
+ * (child 0, child 1); a row is kept iff its (inherited) logit >= *d_tau_logit.
+ * Child: log-scale - FP32(log 1.6), mean + R(q) (exp(s) * z), z ~ N(0, I) from
+ * Philox4x32-10 (Salmon et al., SC'11) with counter (parent, 0, event, child) and key
+ * (seed), Box-Muller on u = ((x >> 8) + 0.5) 2^-24. If the new count exceeds
+ * out_capacity, GS_ERR_CAPACITY is OR-ed into *d_error and nothing is written. */
+gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in,
+                             const uint8_t *split, const uint8_t *clone,
+                             const float *d_tau_logit, gs_params_out_t *out,
+                             const gs_extra_array_t *extra, int32_t n_extra,
+                             int64_t out_capacity, int64_t *d_new_n, int32_t *d_error,
+                             void *ws, size_t ws_bytes, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,58 @@
+"""torch.autograd.Function around the CUDA rasterizer.
+
+forward: gs_project -> gs_bin_sort -> gs_raster_fwd (images of every view, planar,
+concatenated). backward: gs_raster_bwd (record gradients) -> gs_project_bwd
+(parameter gradients, summed over views), with the densification statistic
+accumulated on the way when a DensifyStats object is passed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import rasterizer as R
+
+
+@dataclass
+class DensifyStats:
+    accum: torch.Tensor    # [N] float32
+    count: torch.Tensor    # [N] int32
+
+    @staticmethod
+    def zeros(n, device="cuda"):
+        return DensifyStats(torch.zeros(n, dtype=torch.float32, device=device),
+                            torch.zeros(n, dtype=torch.int32, device=device))
+
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, sh_degree, frame, bg, stats):
+        params = dict(means=means.contiguous(), log_scales=log_scales.contiguous(), quats=quats.contiguous(),
+                      opacity_logits=opacity_logits.contiguous(), sh=sh.contiguous())
+        proj = R.project(params, sh_degree, frame)
+        bins = R.bin_sort(proj, frame)
+        image, T_final, _ = R.raster_fwd(proj, bins, frame, bg)
+        ctx.save_for_backward(*[params[k] for k in R.PARAM_KEYS])
+        ctx.state = (proj, bins, frame, bg, sh_degree, stats, image)
+        ctx.mark_non_differentiable(T_final)
+        return image, T_final
+
+    @staticmethod
+    def backward(ctx, d_image, _d_T):
+        proj, bins, frame, bg, sh_degree, stats, image = ctx.state
+        params = dict(zip(R.PARAM_KEYS, ctx.saved_tensors))
+        rec = R.raster_bwd(proj, bins, frame, image, d_image.contiguous(), bg)
+        acc = cnt = None
+        if stats is not None:
+            acc, cnt = stats.accum, stats.count
+        g = R.project_bwd(params, sh_degree, frame, proj, rec, accum=acc, count=cnt)
+        ctx.state = None
+        return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None, None, None
+
+
+def rasterize(params: dict, sh_degree: int, frame, bg=(0.0, 0.0, 0.0), stats: DensifyStats = None):
+    """Differentiable render of every view of `frame`; returns (image, T_final), the
+    image planar per view and concatenated (see Frame.view_image)."""
+    return _Rasterize.apply(params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
+                            params["sh"], int(sh_degree), frame, tuple(float(b) for b in bg), stats)

@@ -1,0 +1,402 @@
+// Tile binning and depth sort ("tile-based", "depth-sorted" rasterization, Sec.
+// "Preliminary" of the paper).
+//
+// Result: for every global tile, the visible records whose tile rectangle contains
+// it, ordered by (FP32 depth bits, record index), concatenated tile after tile.
+//
+// Instead of one wide radix sort on (tile << 32 | depth) keys over all duplicates,
+// the order is built in two stable stages that give the same permutation:
+//   1. the visible records (one entry each) are compacted in record order and
+//      sorted by their 32-bit depth key (stable LSD radix sort, 4 x 8-bit passes);
+//   2. every record, taken in depth order, emits one entry per tile of its
+//      rectangle, and the entries are stably sorted by tile id alone (ceil(bits/8)
+//      passes of <= 8 bits).
+// A stable sort by tile of a depth-ordered sequence is ordered by (tile, depth,
+// record). Stage 2 moves 8 bytes per duplicate per pass instead of 12 bytes per
+// pass for 5-6 passes.
+//
+// Every count is read from device memory (no host round trip), so the whole
+// sequence can be captured into a CUDA graph. All grids are fixed-size and every
+// block derives its share of the work from the device-side count.
+#include "gs_common.cuh"
+#include "scan.cuh"
+
+namespace gs {
+
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per tile
+constexpr int kRsBins = 256;
+
+// ------------------------------------------------------------------ LSD radix sort pass
+// Digit histograms per block (digit-major: hist[d * G + b]).
+__global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(const uint32_t *__restrict__ keys,
+                                                                const uint32_t *d_n, const uint32_t *d_skip,
+                                                                int shift, uint32_t mask, uint32_t *hist) {
+  __shared__ uint32_t h[kRsWarps][kRsBins];
+  const int G = gridDim.x;
+  const uint64_t n = (d_skip && *d_skip) ? 0 : *d_n;
+  uint64_t begin, end;
+  chunk_of(n, G, kRsTile, begin, end);
+  const int warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRsWarps * kRsBins; d += kRsThreads) (&h[0][0])[d] = 0;
+  __syncthreads();
+  uint64_t i = begin + 4 * threadIdx.x;
+  for (; i + 3 < end; i += 4 * kRsThreads) {
+    const uint4 k = *reinterpret_cast<const uint4 *>(keys + i);
+    atomicAdd(&h[warp][(k.x >> shift) & mask], 1u);
+    atomicAdd(&h[warp][(k.y >> shift) & mask], 1u);
+    atomicAdd(&h[warp][(k.z >> shift) & mask], 1u);
+    atomicAdd(&h[warp][(k.w >> shift) & mask], 1u);
+  }
+  for (; i < end; ++i) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) s += h[w][d];
+    hist[(uint64_t)d * G + blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of hist[256 * G] in place (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t *hist, int G, const uint32_t *d_n,
+                                                        const uint32_t *d_skip) {
+  if (d_skip && *d_skip) return;
+  const uint32_t total = kRsBins * G;
+  const uint32_t per = (total + 1023) / 1024;
+  const uint32_t b = threadIdx.x * per, e = min(total, b + per);
+  uint32_t s = 0;
+  for (uint32_t i = b; i < e; ++i) s += hist[i];
+  __shared__ uint32_t part[1024];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (uint32_t i = b; i < e; ++i) {
+    const uint32_t c = hist[i];
+    hist[i] = run;
+    run += c;
+  }
+}
+
+// Stable scatter. Each warp ranks a contiguous 512-key slice of the tile, 32 keys per
+// step in order, with __match_any_sync; slices are then offset by the warps before
+// them, staged in shared memory in digit order and written out coalesced.
+__global__ void __launch_bounds__(kRsThreads) rs_downsweep_kernel(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const uint32_t *d_n, const uint32_t *d_skip, int shift, uint32_t mask,
+    const uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_keys[kRsTile];
+  __shared__ uint32_t s_vals[kRsTile];
+  __shared__ uint32_t s_whist[kRsWarps][kRsBins + 1];
+  __shared__ uint32_t s_goff[kRsBins];
+  __shared__ uint32_t s_tstart[kRsBins + 1];
+  const int G = gridDim.x;
+  const uint64_t n = (d_skip && *d_skip) ? 0 : *d_n;
+  uint64_t begin, end;
+  chunk_of(n, G, kRsTile, begin, end);
+  if (begin >= end) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) s_goff[d] = hist[(uint64_t)d * G + blockIdx.x];
+  const uint32_t lt_mask = lanemask_lt();
+  for (uint64_t tb = begin; tb < end; tb += kRsTile) {
+    const uint32_t tile_n = (uint32_t)min((uint64_t)kRsTile, end - tb);
+    for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
+    __syncwarp();
+    uint32_t k[kRsItems], v[kRsItems], dig[kRsItems], rank[kRsItems];
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+      const uint32_t li = warp * (32 * kRsItems) + j * 32 + lane;
+      const bool valid = li < tile_n;
+      k[j] = valid ? keys_in[tb + li] : 0u;
+      v[j] = valid ? vals_in[tb + li] : 0u;
+      dig[j] = valid ? ((k[j] >> shift) & mask) : (uint32_t)kRsBins;
+    }
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+      const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+      const uint32_t before = __popc(peers & lt_mask);
+      const uint32_t base = s_whist[warp][dig[j]];
+      __syncwarp();
+      rank[j] = base + before;
+      if (before == 0) s_whist[warp][dig[j]] = base + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int d = threadIdx.x; d < kRsBins + 1; d += kRsThreads) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < kRsWarps; ++w) {
+        const uint32_t c = s_whist[w][d];
+        s_whist[w][d] = run;
+        run += c;
+      }
+      if (d < kRsBins) tot = run;
+    }
+    uint32_t all;
+    const uint32_t start = block_exclusive_scan<uint32_t>(tot, &all);
+    s_tstart[threadIdx.x] = start;
+    if (threadIdx.x == 0) s_tstart[kRsBins] = all;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRsItems; ++j) {
+      const uint32_t pos = s_tstart[dig[j]] + s_whist[warp][dig[j]] + rank[j];
+      s_keys[pos] = k[j];
+      s_vals[pos] = v[j];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tile_n; i += kRsThreads) {
+      const uint32_t key = s_keys[i];
+      const uint32_t d = (key >> shift) & mask;
+      const uint32_t gpos = s_goff[d] + (i - s_tstart[d]);
+      if (keys_out) keys_out[gpos] = key;
+      vals_out[gpos] = s_vals[i];
+    }
+    __syncthreads();
+    s_goff[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ bin/sort functors
+struct VisibleCompact {
+  const int32_t *radius;
+  const float *depth;
+  uint64_t n;
+  uint32_t *keys, *vals, *n_vis;
+  __device__ uint64_t count() const { return n; }
+  __device__ uint32_t value(uint64_t i) const { return radius[i] > 0 ? 1u : 0u; }
+  __device__ void emit(uint64_t i, uint64_t pre, uint32_t v) const {
+    if (v) {
+      keys[pre] = __float_as_uint(depth[i]);
+      vals[pre] = (uint32_t)i;
+    }
+  }
+  __device__ void total(uint64_t t) const { *n_vis = (uint32_t)t; }
+};
+
+__device__ __forceinline__ uint32_t rect_area(const uint16_t *rect, uint32_t r) {
+  const uint2 q = reinterpret_cast<const uint2 *>(rect)[r];
+  const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
+  return (x1 - x0) * (y1 - y0);
+}
+
+struct TouchedOffsets {
+  const uint16_t *rect;
+  const uint32_t *order;      // records in depth order
+  const uint32_t *n_vis;
+  uint32_t *offsets;
+  uint64_t capacity;
+  uint32_t *m_total;          // M (clamped to 2^32-1)
+  uint32_t *overflow;
+  int64_t *d_count;
+  int32_t *d_error;
+  __device__ uint64_t count() const { return *n_vis; }
+  __device__ uint32_t value(uint64_t k) const { return rect_area(rect, order[k]); }
+  __device__ void emit(uint64_t k, uint64_t pre, uint32_t) const {
+    if (pre <= 0xffffffffull) offsets[k] = (uint32_t)pre;
+  }
+  __device__ void total(uint64_t t) const {
+    *d_count = (int64_t)t;
+    const bool over = t > capacity;
+    *overflow = over ? 1u : 0u;
+    *m_total = over ? 0u : (uint32_t)t;
+    if (over && d_error) atomicOr(d_error, (int32_t)GS_ERR_CAPACITY);
+  }
+};
+
+// One thread per depth-ordered record: write (tile id, record) for each tile of its rect.
+__global__ void emit_kernel(const uint16_t *__restrict__ rect, const uint32_t *__restrict__ order,
+                            const uint32_t *__restrict__ offsets, const uint32_t *n_vis, const uint32_t *overflow,
+                            const int32_t *__restrict__ view_of_record_tile_offset_unused,
+                            const gs_camera_t *__restrict__ cams, int n_views, int64_t n_per_view,
+                            uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
+  if (*overflow) return;
+  const uint32_t nv = *n_vis;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += gridDim.x * blockDim.x) {
+    const uint32_t r = order[k];
+    const uint2 q = reinterpret_cast<const uint2 *>(rect)[r];
+    const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
+    const int v = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
+    const uint32_t toff = (uint32_t)cams[v].tile_offset;
+    const uint32_t gx = (uint32_t)cams[v].grid_x;
+    uint32_t o = offsets[k];
+    for (uint32_t ty = y0; ty < y1; ++ty)
+      for (uint32_t tx = x0; tx < x1; ++tx) {
+        dkeys[o] = toff + ty * gx + tx;
+        dvals[o] = r;
+        ++o;
+      }
+  }
+}
+
+// ranges[t] = [first index with key >= t, first index with key > t) over the sorted keys.
+__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *m_total, const uint32_t *overflow,
+                              int n_tiles, uint2 *__restrict__ ranges) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (*overflow) {
+    for (int64_t t = tid; t < n_tiles; t += stride) ranges[t] = make_uint2(0u, 0u);
+    return;
+  }
+  const uint32_t M = *m_total;
+  for (int64_t i = tid; i <= (int64_t)M; i += stride) {
+    const int64_t prev = i > 0 ? (int64_t)keys[i - 1] : -1;
+    const int64_t cur = i < (int64_t)M ? (int64_t)keys[i] : (int64_t)n_tiles;
+    for (int64_t t = prev + 1; t <= cur && t < n_tiles; ++t) ranges[t].x = (uint32_t)i;
+    for (int64_t t = prev < 0 ? 0 : prev; t < cur && t < n_tiles; ++t) ranges[t].y = (uint32_t)i;
+  }
+}
+
+__global__ void keys64_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ vals,
+                              const float *__restrict__ depth, const uint32_t *m_total, const uint32_t *overflow,
+                              uint64_t *__restrict__ keys) {
+  if (*overflow) return;
+  const uint32_t M = *m_total;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
+    keys[i] = ((uint64_t)tiles[i] << 32) | __float_as_uint(depth[vals[i]]);
+}
+
+// ------------------------------------------------------------------ host side
+struct BinWs {
+  uint32_t *vk0, *vv0, *vk1, *vv1;   // visible records: depth keys / record ids (double buffered)
+  uint32_t *offsets;                 // duplicate offsets in depth order
+  uint32_t *dk0, *dk1, *dv1;         // duplicate tile keys (double buffered) + second value buffer
+  uint64_t *block_sums;
+  uint32_t *hist;
+  uint32_t *counters;                // [0] n_vis, [1] M, [2] overflow
+  size_t bytes;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
+  BinWs w{};
+  char *p = static_cast<char *>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void * {
+    void *q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  w.vk0 = (uint32_t *)take(4 * (size_t)R + 16);
+  w.vv0 = (uint32_t *)take(4 * (size_t)R + 16);
+  w.vk1 = (uint32_t *)take(4 * (size_t)R + 16);
+  w.vv1 = (uint32_t *)take(4 * (size_t)R + 16);
+  w.offsets = (uint32_t *)take(4 * (size_t)R + 16);
+  w.dk0 = (uint32_t *)take(4 * (size_t)cap + 16);
+  w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
+  w.dv1 = (uint32_t *)take(4 * (size_t)cap + 16);
+  w.block_sums = (uint64_t *)take(8 * kMaxBlocks);
+  w.hist = (uint32_t *)take(4 * (size_t)kRsBins * kMaxBlocks);
+  w.counters = (uint32_t *)take(64);
+  w.bytes = off;
+  return w;
+}
+
+
+// Stable LSD radix sort of (key, val) pairs on bits [0, n_bits), ping-ponging between
+// buffer 0 and 1; returns in *in_b0 whether the result is in buffer 0.
+static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *d_n,
+                              const uint32_t *d_skip, int n_bits, bool keep_keys, uint32_t *hist, int G,
+                              cudaStream_t s, bool *in_b0) {
+  const int passes = (n_bits + 7) / 8;
+  const int bits = (n_bits + passes - 1) / passes;
+  bool cur0 = true;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * bits;
+    const int nb = (shift + bits > n_bits) ? n_bits - shift : bits;
+    const uint32_t mask = (1u << nb) - 1u;
+    uint32_t *ki = cur0 ? k0 : k1, *vi = cur0 ? v0 : v1, *ko = cur0 ? k1 : k0, *vo = cur0 ? v1 : v0;
+    rs_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, d_n, d_skip, shift, mask, hist);
+    GS_LAUNCH_CHECK();
+    rs_scan_kernel<<<1, 1024, 0, s>>>(hist, G, d_n, d_skip);
+    GS_LAUNCH_CHECK();
+    const bool last = p == passes - 1;
+    rs_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, (last && !keep_keys) ? nullptr : ko, vo, d_n, d_skip,
+                                                 shift, mask, hist);
+    GS_LAUNCH_CHECK();
+    cur0 = !cur0;
+  }
+  *in_b0 = cur0;
+  return GS_OK;
+}
+
+static int bits_for(uint32_t max_value) {
+  int b = 1;
+  while (b < 32 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const gs_frame_t *frame) {
+  (void)frame;
+  if (n_records < 0 || dup_capacity < 0) return 0;
+  return bin_ws_layout(nullptr, n_records, dup_capacity).bytes;
+}
+
+extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *frame, gs_bins_t *bins, void *ws,
+                                   size_t ws_bytes, int32_t *d_error, gs_stream_t stream) {
+  if (!proj || !frame || !bins || !ws || !frame->cams_dev || frame->n_views <= 0 || frame->n_tiles <= 0)
+    return GS_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->ranges || !bins->d_count || bins->capacity < 0 || bins->capacity >= (1ll << 31))
+    return GS_ERR_INVALID_ARG;
+  const int64_t R = proj->n_records;
+  if (R < 0 || R >= (1ll << 31) || R % frame->n_views != 0) return GS_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GS_ERR_INVALID_ARG;
+  const BinWs w = bin_ws_layout(ws, R, bins->capacity);
+  if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const int G = scan_blocks();
+  uint32_t *n_vis = w.counters + 0, *m_total = w.counters + 1, *overflow = w.counters + 2;
+  GS_CUDA_TRY(cudaMemsetAsync(w.counters, 0, 64, s));
+
+  // 1. compact visible records (record order) with their FP32 depth bits as keys
+  VisibleCompact vc{proj->radius, proj->depth, (uint64_t)R, w.vk0, w.vv0, n_vis};
+  if (gs_status_t st = run_scan(vc, w.block_sums, G, s)) return st;
+  // 2. stable sort by depth
+  bool in0 = true;
+  if (gs_status_t st = radix_sort(w.vk0, w.vv0, w.vk1, w.vv1, n_vis, nullptr, 32, false, w.hist, G, s, &in0)) return st;
+  const uint32_t *order = in0 ? w.vv0 : w.vv1;
+  // 3. duplicate offsets in depth order, M and the capacity check
+  TouchedOffsets to{proj->rect, order, n_vis, w.offsets, (uint64_t)bins->capacity, m_total, overflow,
+                    bins->d_count, d_error};
+  if (gs_status_t st = run_scan(to, w.block_sums, G, s)) return st;
+  // 4. emit (tile, record) in depth order, into the buffer the tile sort ends in
+  const int tile_bits = bits_for((uint32_t)(frame->n_tiles - 1));
+  const int passes = (tile_bits + 7) / 8;
+  uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
+  const bool emit_to_A = (passes % 2) == 0;
+  const int64_t n_per_view = R / frame->n_views;
+  const int eg = num_sms() * 8;
+  emit_kernel<<<eg, 256, 0, s>>>(proj->rect, order, w.offsets, n_vis, overflow, nullptr, frame->cams_dev,
+                                 frame->n_views, n_per_view, emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
+  GS_LAUNCH_CHECK();
+  // 5. stable sort by tile id
+  bool res0 = true;
+  if (emit_to_A) {
+    if (gs_status_t st = radix_sort(A_k, A_v, B_k, B_v, m_total, overflow, tile_bits, true, w.hist, G, s, &res0)) return st;
+  } else {
+    if (gs_status_t st = radix_sort(B_k, B_v, A_k, A_v, m_total, overflow, tile_bits, true, w.hist, G, s, &res0)) return st;
+    res0 = !res0;
+  }
+  // 6. per-tile ranges (and optional 64-bit keys)
+  ranges_kernel<<<eg, 256, 0, s>>>(A_k, m_total, overflow, frame->n_tiles, reinterpret_cast<uint2 *>(bins->ranges));
+  GS_LAUNCH_CHECK();
+  if (bins->keys) {
+    keys64_kernel<<<eg, 256, 0, s>>>(A_k, A_v, proj->depth, m_total, overflow, bins->keys);
+    GS_LAUNCH_CHECK();
+  }
+  return GS_OK;
+}

@@ -1,0 +1,410 @@
+// Front-to-back alpha compositing (the paper's Eq. 2) and its gradient.
+//
+// One CTA per tile, two horizontally adjacent pixels per thread. The tile's
+// depth-ordered list is consumed in batches of one record per thread, staged in
+// shared memory; a pixel stops before the entry that would drive its
+// transmittance below 1e-4 and the CTA leaves once every pixel has stopped.
+//
+// The backward pass re-walks the list front to back with exactly the forward's
+// FP32 decisions (no stored stop index) and needs, per pixel, only <dL/dout, out>:
+//   dL/dsigma_i = T_i <c_i, g> - (<out, g> - sum_{j<=i} <c_j, g> sigma_j T_j) / (1 - sigma_i).
+// The 9 per-(pixel, Gaussian) gradient terms are summed over the thread's two
+// pixels in registers, across the warp with a transposing shuffle reduction, across
+// the CTA's warps in shared memory, and then added once per (tile, record) to the
+// record gradients with vector reductions.
+#include "gs_common.cuh"
+
+namespace gs {
+
+struct TileCoord {
+  int view, tx, ty, W, H;
+  int64_t pix_off;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const gs_camera_t *cams, int n_views, int tile) {
+  TileCoord c;
+  c.view = view_of_tile(cams, n_views, tile);
+  const gs_camera_t &cam = cams[c.view];
+  const int lt = tile - cam.tile_offset;
+  c.tx = lt % cam.grid_x;
+  c.ty = lt / cam.grid_x;
+  c.W = cam.width;
+  c.H = cam.height;
+  c.pix_off = cam.pixel_offset;
+  return c;
+}
+
+// COUNT: instead of the image, write per pixel (entries examined up to and including
+// the one that triggers the cut-off, entries composited) to counts[2 * pixel].
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
+    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
+    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
+    int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
+    uint32_t *__restrict__ stop_out, uint32_t *__restrict__ counts) {
+  constexpr int NT = TW * TH / 2, HW = TW / 2;
+  __shared__ float2 s_xy[NT];
+  __shared__ float4 s_co[NT];
+  __shared__ float4 s_rgb[NT];
+  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int t = threadIdx.x;
+  const int py = tc.ty * TH + t / HW;
+  const int px = tc.tx * TW + 2 * (t % HW);
+  const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
+  const float fy = (float)py + 0.5f, fx0 = (float)px + 0.5f, fx1 = (float)px + 1.5f;
+  float T0 = 1.f, T1 = 1.f;
+  float r0 = 0.f, g0 = 0.f, b0 = 0.f, r1 = 0.f, g1 = 0.f, b1 = 0.f;
+  uint32_t st0 = 0, st1 = 0;
+  uint32_t ex0 = 0, ex1 = 0, nc0 = 0, nc1 = 0;
+  bool done0 = !in0, done1 = !in1;
+  const uint2 rg = ranges[blockIdx.x];
+  const int n = (int)(rg.y - rg.x);
+  for (int base = 0; base < n; base += NT) {
+    if (__syncthreads_count(!(done0 && done1)) == 0) break;
+    if (base + t < n) {
+      const uint32_t r = vals[rg.x + base + t];
+      s_xy[t] = mean2d[r];
+      s_co[t] = stage_conic(conic_o[r]);
+      s_rgb[t] = rgb[r];
+    }
+    __syncthreads();
+    if (__all_sync(0xffffffffu, done0 && done1)) continue;
+    const int cnt = min(NT, n - base);
+    for (int j = 0; j < cnt; ++j) {
+      const float2 xy = s_xy[j];
+      const float4 co = s_co[j];
+      if (!done0) {
+        if (COUNT) ++ex0;
+        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx0, fy);
+        if (f.power <= 0.f && f.alpha >= kAlphaMin) {
+          const float Tn = __fmul_rn(T0, __fsub_rn(1.f, f.alpha));
+          if (Tn < kTMin) {
+            done0 = true;
+          } else {
+            if (COUNT) ++nc0;
+            const float4 c = s_rgb[j];
+            const float w = f.alpha * T0;
+            r0 = fmaf(c.x, w, r0); g0 = fmaf(c.y, w, g0); b0 = fmaf(c.z, w, b0);
+            T0 = Tn;
+            st0 = base + j + 1;
+          }
+        }
+      }
+      if (!done1) {
+        if (COUNT) ++ex1;
+        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx1, fy);
+        if (f.power <= 0.f && f.alpha >= kAlphaMin) {
+          const float Tn = __fmul_rn(T1, __fsub_rn(1.f, f.alpha));
+          if (Tn < kTMin) {
+            done1 = true;
+          } else {
+            if (COUNT) ++nc1;
+            const float4 c = s_rgb[j];
+            const float w = f.alpha * T1;
+            r1 = fmaf(c.x, w, r1); g1 = fmaf(c.y, w, g1); b1 = fmaf(c.z, w, b1);
+            T1 = Tn;
+            st1 = base + j + 1;
+          }
+        }
+      }
+    }
+  }
+  const int64_t p0 = (int64_t)py * tc.W + px;
+  if (COUNT) {
+    if (in0) reinterpret_cast<uint2 *>(counts)[tc.pix_off + p0] = make_uint2(ex0, nc0);
+    if (in1) reinterpret_cast<uint2 *>(counts)[tc.pix_off + p0 + 1] = make_uint2(ex1, nc1);
+    return;
+  }
+  const int64_t plane = (int64_t)tc.W * tc.H;
+  float *img = image + 3 * tc.pix_off;
+  if (in0) {
+    img[p0] = fmaf(T0, bg0, r0);
+    img[plane + p0] = fmaf(T0, bg1, g0);
+    img[2 * plane + p0] = fmaf(T0, bg2, b0);
+    T_final[tc.pix_off + p0] = T0;
+    if (stop_out) stop_out[tc.pix_off + p0] = st0;
+  }
+  if (in1) {
+    img[p0 + 1] = fmaf(T1, bg0, r1);
+    img[plane + p0 + 1] = fmaf(T1, bg1, g1);
+    img[2 * plane + p0 + 1] = fmaf(T1, bg2, b1);
+    T_final[tc.pix_off + p0 + 1] = T1;
+    if (stop_out) stop_out[tc.pix_off + p0 + 1] = st1;
+  }
+}
+
+// Sum 9 per-lane values over the warp and add the totals to acc[0..8] in shared
+// memory. Values 0..7 are reduced by a transposing butterfly (each step exchanges
+// half of the remaining values), value 8 by a plain butterfly: 14 shuffles.
+__device__ __forceinline__ void warp_reduce9_add(const float v[9], float *acc, int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float a[4], b[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = b4 ? v[k] : v[k + 4];
+    const float keep = b4 ? v[k + 4] : v[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b3 ? a[k] : a[k + 2];
+    const float keep = b3 ? a[k + 2] : a[k];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float c;
+  {
+    const float send = b2 ? b[0] : b[1];
+    const float keep = b2 ? b[1] : b[0];
+    c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  float e = v[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((lane & 3) == 0) atomicAdd(&acc[lane >> 2], c);   // value index 4*b4 + 2*b3 + b2
+  if (lane == 0) atomicAdd(&acc[8], e);
+}
+
+struct PixBwd {
+  float fx, T, S, K, d0, d1, d2;
+  bool done;
+};
+
+// One pixel's contribution of the current Gaussian, accumulated into v[9] =
+// (d_u, d_v, d_A, d_B, d_C, d_o, d_r, d_g, d_b).
+// co = staged (A, beta, gamma, o); B = the conic's off-diagonal entry.
+__device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, const float4 co, float B,
+                                        const float4 c, float *v) {
+  if (p.done) return false;
+  const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, p.fx, fy);
+  if (!(f.power <= 0.f && f.alpha >= kAlphaMin)) return false;
+  const float one_m = __fsub_rn(1.f, f.alpha);
+  const float Tn = __fmul_rn(p.T, one_m);
+  if (Tn < kTMin) {
+    p.done = true;
+    return false;
+  }
+  const float w = f.alpha * p.T;
+  const float cd = c.x * p.d0 + c.y * p.d1 + c.z * p.d2;
+  p.S = fmaf(cd, w, p.S);
+  const float dLda = p.T * cd - __fdividef(p.K - p.S, one_m);
+  p.T = Tn;
+  v[6] = fmaf(p.d0, w, v[6]);
+  v[7] = fmaf(p.d1, w, v[7]);
+  v[8] = fmaf(p.d2, w, v[8]);
+  if (f.raw <= kAlphaMax) {
+    v[5] = fmaf(f.G, dLda, v[5]);
+    const float dP = dLda * f.raw;
+    // dP/du = -(A dx + B dy) = -A t, dP/dv = -(B dx + C dy) = -(B t + gamma dy)
+    v[0] -= dP * (co.x * f.t);
+    v[1] -= dP * fmaf(B, f.t, co.z * f.dy);
+    v[2] -= 0.5f * dP * f.dx * f.dx;
+    v[3] -= dP * f.dx * f.dy;
+    v[4] -= 0.5f * dP * f.dy * f.dy;
+  }
+  return true;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
+    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
+    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
+    int n_views, const float *__restrict__ image, const float *__restrict__ d_image, float *__restrict__ g_mean2d,
+    float *__restrict__ g_co, float *__restrict__ g_rgb) {
+  constexpr int NT = TW * TH / 2, HW = TW / 2;
+  __shared__ float2 s_xy[NT];
+  __shared__ float4 s_co[NT];
+  __shared__ float4 s_rgb[NT];
+  __shared__ uint32_t s_rec[NT];
+  __shared__ float s_B[NT];
+  __shared__ float s_acc[NT * 9];
+  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int t = threadIdx.x, lane = t & 31;
+  const int py = tc.ty * TH + t / HW;
+  const int px = tc.tx * TW + 2 * (t % HW);
+  const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
+  const float fy = (float)py + 0.5f;
+  const int64_t plane = (int64_t)tc.W * tc.H;
+  const int64_t p0 = (int64_t)py * tc.W + px;
+  const float *img = image + 3 * tc.pix_off;
+  const float *dim = d_image + 3 * tc.pix_off;
+  PixBwd q0{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in0};
+  PixBwd q1{(float)px + 1.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in1};
+  if (in0) {
+    q0.d0 = dim[p0]; q0.d1 = dim[plane + p0]; q0.d2 = dim[2 * plane + p0];
+    q0.K = q0.d0 * img[p0] + q0.d1 * img[plane + p0] + q0.d2 * img[2 * plane + p0];
+  }
+  if (in1) {
+    q1.d0 = dim[p0 + 1]; q1.d1 = dim[plane + p0 + 1]; q1.d2 = dim[2 * plane + p0 + 1];
+    q1.K = q1.d0 * img[p0 + 1] + q1.d1 * img[plane + p0 + 1] + q1.d2 * img[2 * plane + p0 + 1];
+  }
+  const uint2 rg = ranges[blockIdx.x];
+  const int n = (int)(rg.y - rg.x);
+  for (int base = 0; base < n; base += NT) {
+    if (__syncthreads_count(!(q0.done && q1.done)) == 0) break;
+    const int cnt = min(NT, n - base);
+    if (t < cnt) {
+      const uint32_t r = vals[rg.x + base + t];
+      s_rec[t] = r;
+      s_xy[t] = mean2d[r];
+      const float4 co = conic_o[r];
+      s_co[t] = stage_conic(co);
+      s_B[t] = co.y;
+      s_rgb[t] = rgb[r];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s_acc[k * NT + t] = 0.f;
+    __syncthreads();
+    if (!__all_sync(0xffffffffu, q0.done && q1.done)) {
+      for (int j = 0; j < cnt; ++j) {
+        const float2 xy = s_xy[j];
+        const float4 co = s_co[j];
+        const float4 c = s_rgb[j];
+        const float B = s_B[j];
+        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool any = pix_bwd(q0, fy, xy, co, B, c, v);
+        any |= pix_bwd(q1, fy, xy, co, B, c, v);
+        if (__any_sync(0xffffffffu, any)) warp_reduce9_add(v, s_acc + j * 9, lane);
+      }
+    }
+    __syncthreads();
+    if (t < cnt) {
+      const float *a = s_acc + t * 9;
+      const float u0 = a[0], u1 = a[1], c0 = a[2], c1 = a[3], c2 = a[4], c3 = a[5], k0 = a[6], k1 = a[7], k2 = a[8];
+      if (u0 != 0.f || u1 != 0.f || c0 != 0.f || c1 != 0.f || c2 != 0.f || c3 != 0.f || k0 != 0.f || k1 != 0.f ||
+          k2 != 0.f) {
+        const uint32_t r = s_rec[t];
+        red_add_v2(g_mean2d + 2 * (size_t)r, u0, u1);
+        red_add_v4(g_co + 4 * (size_t)r, c0, c1, c2, c3);
+        red_add_v4(g_rgb + 4 * (size_t)r, k0, k1, k2, 0.f);
+      }
+    }
+  }
+}
+
+__global__ void l1_loss_grad_kernel(const gs_camera_t *__restrict__ cams, const float *__restrict__ image,
+                                    const float *__restrict__ target, float *__restrict__ d_image, float *loss) {
+  const int v = blockIdx.y;
+  const gs_camera_t &cam = cams[v];
+  const int64_t n = 3ll * cam.width * cam.height;
+  const int64_t off = 3 * cam.pixel_offset;
+  const float inv = 1.f / (float)n;
+  float acc = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = image[off + i] - target[off + i];
+    d_image[off + i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+    acc += fabsf(d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += ws[i];
+    atomicAdd(loss + v, s * inv);
+  }
+}
+
+template <int TW, int TH, bool COUNT = false>
+static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                              const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
+                              cudaStream_t s, uint32_t *counts = nullptr) {
+  raster_fwd_kernel<TW, TH, COUNT><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
+      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
+      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
+      frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,
+      cfg->store_stop ? stop : nullptr, counts);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+template <int TW, int TH>
+static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                              const float *image, const float *d_image, gs_rec_grads_t *g, cudaStream_t s) {
+  const size_t R = (size_t)proj->n_records;
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
+  raster_bwd_kernel<TW, TH><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
+      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
+      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
+      frame->cams_dev, frame->n_views, image, d_image, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+static bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int32_t gs_tile_supported(int32_t tw, int32_t th) {
+  return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 16 && th == 32) || (tw == 32 && th == 16);
+}
+
+extern "C" gs_status_t gs_raster_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                     const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
+                                     gs_stream_t stream) {
+  if (!proj || !bins || !frame || !cfg || !image || !T_final || !frame->cams_dev || frame->n_tiles <= 0)
+    return GS_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->ranges || !proj->mean2d || !a16(proj->conic_opacity) || !a16(proj->rgb))
+    return GS_ERR_INVALID_ARG;
+  if (cfg->store_stop && !stop) return GS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_fwd<16, 16>(proj, bins, frame, cfg, image, T_final, stop, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_fwd<8, 8>(proj, bins, frame, cfg, image, T_final, stop, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_fwd<16, 32>(proj, bins, frame, cfg, image, T_final, stop, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_fwd<32, 16>(proj, bins, frame, cfg, image, T_final, stop, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                     const gs_raster_cfg_t *cfg, const float *image, const float *d_image,
+                                     gs_rec_grads_t *grads, gs_stream_t stream) {
+  if (!proj || !bins || !frame || !cfg || !image || !d_image || !grads || !frame->cams_dev || frame->n_tiles <= 0)
+    return GS_ERR_INVALID_ARG;
+  if (!grads->d_mean2d || !a16(grads->d_conic_opacity) || !a16(grads->d_rgb) || !grads->d_conic_opacity ||
+      !grads->d_rgb || ((reinterpret_cast<uintptr_t>(grads->d_mean2d) & 7u) != 0))
+    return GS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd<16, 16>(proj, bins, frame, image, d_image, grads, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, grads, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, grads, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" gs_status_t gs_raster_count(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                       uint32_t *counts, gs_stream_t stream) {
+  if (!proj || !bins || !frame || !counts || !frame->cams_dev || frame->n_tiles <= 0 || !bins->vals ||
+      !bins->ranges || !a16(proj->conic_opacity) || !a16(proj->rgb) ||
+      (reinterpret_cast<uintptr_t>(counts) & 7u) != 0)
+    return GS_ERR_INVALID_ARG;
+  gs_raster_cfg_t cfg{};
+  cudaStream_t s = as_stream(stream);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_fwd<16, 16, true>(proj, bins, frame, &cfg, nullptr, nullptr, nullptr, s, counts);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_fwd<8, 8, true>(proj, bins, frame, &cfg, nullptr, nullptr, nullptr, s, counts);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_fwd<16, 32, true>(proj, bins, frame, &cfg, nullptr, nullptr, nullptr, s, counts);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_fwd<32, 16, true>(proj, bins, frame, &cfg, nullptr, nullptr, nullptr, s, counts);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" gs_status_t gs_l1_loss_grad(const gs_frame_t *frame, const float *image, const float *target,
+                                       float *d_image, float *loss_dev, gs_stream_t stream) {
+  if (!frame || !frame->cams_dev || frame->n_views <= 0 || !image || !target || !d_image || !loss_dev)
+    return GS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  GS_CUDA_TRY(cudaMemsetAsync(loss_dev, 0, sizeof(float) * frame->n_views, s));
+  const int64_t per_view = 3ll * frame->max_width * frame->max_height;
+  int bx = (int)((per_view + 255) / 256);
+  const int cap = num_sms() * 4;
+  if (bx > cap) bx = cap;
+  if (bx < 1) bx = 1;
+  l1_loss_grad_kernel<<<dim3(bx, frame->n_views), 256, 0, s>>>(frame->cams_dev, image, target, d_image, loss_dev);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}

@@ -1,0 +1,114 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every entry
+point include/gs.h declares; the ctypes mirror has the C layout; host-only entry
+points and host-side argument checks work on the CPU (no device call is made)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2507_20239_gb300 import build as gbuild
+from paper_2507_20239_gb300 import _abi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return _abi.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for want in ("gs_project", "gs_bin_sort", "gs_raster_fwd", "gs_raster_bwd", "gs_project_bwd",
+                 "gs_densify_accum", "gs_densify_select", "gs_densify_apply", "gs_l1_loss_grad"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(_abi.SIGNATURES)
+
+
+STRUCTS = {
+    "gs_camera_t": (_abi.GsCamera, ["R", "t", "fx", "width", "near_plane", "grid_x", "tile_offset", "pixel_offset"]),
+    "gs_frame_t": (_abi.GsFrame, ["cams_dev", "n_views", "n_tiles", "n_pixels", "max_height"]),
+    "gs_params_t": (_abi.GsParams, ["means", "sh", "n", "sh_degree", "sh_stride"]),
+    "gs_proj_t": (_abi.GsProj, ["mean2d", "clamped", "n_records"]),
+    "gs_bins_t": (_abi.GsBins, ["vals", "keys", "ranges", "d_count", "capacity"]),
+    "gs_raster_cfg_t": (_abi.GsRasterCfg, ["bg", "store_stop"]),
+    "gs_rec_grads_t": (_abi.GsRecGrads, ["d_mean2d", "d_rgb"]),
+    "gs_param_grads_t": (_abi.GsParamGrads, ["d_means", "d_sh"]),
+    "gs_densify_cfg_t": (_abi.GsDensifyCfg, ["mode", "prune_upper_logit", "prune_ratio", "seed", "event"]),
+    "gs_extra_array_t": (_abi.GsExtraArray, ["src", "dst", "width"]),
+    "gs_params_out_t": (_abi.GsParamsOut, ["means", "sh"]),
+}
+
+
+def test_ctypes_layout_matches_c_compiler():
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
+    for name, (_, fields) in STRUCTS.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        parts = line.split()
+        cls = STRUCTS[parts[0]][0]
+        if parts[1] == "size":
+            assert C.sizeof(cls) == int(parts[2]), line
+        else:
+            assert getattr(cls, parts[1]).offset == int(parts[2]), line
+
+
+def test_host_only_entry_points(lib):
+    assert lib.gs_status_str(0) == b"ok"
+    assert b"sm_103a" in lib.gs_version()
+    assert lib.gs_tile_supported(16, 16) and lib.gs_tile_supported(8, 8) and lib.gs_tile_supported(16, 32)
+    assert not lib.gs_tile_supported(12, 12)
+    cams = (_abi.GsCamera * 3)()
+    for i, (w, h) in enumerate([(312, 207), (623, 413), (1246, 826)]):
+        cams[i].width, cams[i].height = w, h
+        cams[i].fx = cams[i].fy = 100.0
+        cams[i].near_plane = 0.2
+    fr = _abi.GsFrame()
+    assert lib.gs_frame_init(cams, 3, 16, 16, C.byref(fr)) == 0
+    assert [cams[i].grid_x for i in range(3)] == [20, 39, 78]
+    assert [cams[i].grid_y for i in range(3)] == [13, 26, 52]
+    assert [cams[i].tile_offset for i in range(3)] == [0, 260, 260 + 1014]
+    assert fr.n_tiles == 260 + 1014 + 4056
+    assert fr.n_pixels == 312 * 207 + 623 * 413 + 1246 * 826
+    assert [cams[i].pixel_offset for i in range(3)] == [0, 312 * 207, 312 * 207 + 623 * 413]
+    assert lib.gs_frame_init(cams, 3, 12, 12, C.byref(fr)) == 1
+    assert lib.gs_bin_sort_workspace_size(1000, 5000, C.byref(fr)) > 4 * 5000 * 3
+    assert lib.gs_densify_workspace_size(1000) > 0
+
+
+def test_host_argument_checks_return_invalid_arg(lib):
+    fr = _abi.GsFrame()
+    assert lib.gs_project(None, C.byref(fr), None, None) == 1
+    assert lib.gs_bin_sort(None, None, None, None, 0, None, None) == 1
+    assert lib.gs_raster_fwd(None, None, None, None, None, None, None, None) == 1
+    assert lib.gs_raster_bwd(None, None, None, None, None, None, None, None) == 1
+    assert lib.gs_project_bwd(None, None, None, None, None, None, None, None) == 1
+    assert lib.gs_densify_accum(None, None, None, 0, None, None, None) == 1
+    assert lib.gs_l1_loss_grad(None, None, None, None, None, None) == 1
+    p = _abi.GsParams()
+    p.n, p.sh_degree, p.sh_stride = 10, 4, 25       # degree 4 is not supported
+    assert lib.gs_project(C.byref(p), C.byref(fr), None, None) == 1

@@ -1,0 +1,107 @@
+"""gs_bin_sort: keys, order and per-tile ranges bit-exact against the oracle's
+definition (sort by tile, FP32 depth bits, record index) on the same FP32 records."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import project as oproj
+from oracle import raster as oras
+from paper_2507_20239_gb300 import rasterizer as R
+from paper_2507_20239_gb300 import synth
+from tests.gs_fixtures import oracle_records_fp32, records_to_gpu, scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _synthetic_records(seed, n, cams, tile):
+    recs = []
+    for v, cam in enumerate(cams):
+        m2, dep, rad = synth.random_records(seed + v, n, cam.width, cam.height)
+        gx, gy = oproj.tile_grid(cam.width, cam.height, *tile)
+        rect = oproj.tile_rect(m2, rad, tile[0], tile[1], gx, gy)
+        area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
+        rad = np.where(area > 0, rad, 0).astype(np.int32)
+        rect[area <= 0] = 0
+        z3 = np.zeros((n, 3), np.float32)
+        recs.append(dict(mean2d=m2, depth=np.where(rad > 0, dep, 0).astype(np.float32), radius=rad, rect=rect,
+                         conic=z3, opacity=np.zeros(n, np.float32), rgb=z3, grid=(gx, gy)))
+    return recs
+
+
+def _oracle_bins(recs, frame):
+    rect = np.concatenate([r["rect"] for r in recs])
+    depth = np.concatenate([r["depth"] for r in recs])
+    n = recs[0]["rect"].shape[0]
+    toff = np.repeat([frame.views[v][3] for v in range(len(recs))], n).astype(np.int64)
+    gxs = np.repeat([frame.views[v][4] for v in range(len(recs))], n).astype(np.int64)
+    return oras.bin_and_sort(rect, depth, toff, gxs, frame.n_tiles)
+
+
+def _check(recs, cams, tile, capacity=None):
+    frame = R.Frame(cams, tile=tile)
+    proj = records_to_gpu(recs)
+    keys, vals, ranges = _oracle_bins(recs, frame)
+    bins = R.bin_sort(proj, frame, capacity=capacity, want_keys=True)
+    torch.cuda.synchronize()
+    M = int(bins.count.item())
+    assert M == len(vals)
+    assert np.array_equal(bins.vals[:M].cpu().numpy().view(np.uint32), vals)
+    assert np.array_equal(bins.keys[:M].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(bins.ranges.cpu().numpy().view(np.uint32), ranges)
+    return M
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
+def test_bin_sort_synthetic_records_single_view(tile):
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 100., 100., 150., 100., 300, 200)
+    recs = _synthetic_records(0, 20000, [cam], tile)
+    assert _check(recs, [cam], tile) > 20000
+
+
+def test_bin_sort_mixed_resolution_views():
+    cams, _ = synth.mixed_resolution_cameras(6)
+    recs = _synthetic_records(10, 30000, cams, (16, 16))
+    _check(recs, cams, (16, 16))
+
+
+def test_bin_sort_edge_cases():
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 50., 50., 17., 9., 35, 19)
+    # all culled -> empty lists
+    recs = _synthetic_records(3, 500, [cam], (16, 16))
+    for k in ("radius", "depth"):
+        recs[0][k][:] = 0
+    recs[0]["rect"][:] = 0
+    assert _check(recs, [cam], (16, 16)) == 0
+    # a single record, and all records at exactly the same depth (ties -> record order)
+    recs = _synthetic_records(4, 1, [cam], (16, 16))
+    recs[0]["radius"][:] = 50
+    recs[0]["rect"][0] = [0, 0, 3, 2]
+    recs[0]["depth"][:] = 1.0
+    assert _check(recs, [cam], (16, 16)) == 6
+    recs = _synthetic_records(5, 5000, [cam], (16, 16))
+    recs[0]["depth"][recs[0]["radius"] > 0] = 2.5
+    _check(recs, [cam], (16, 16))
+
+
+def test_bin_sort_capacity_overflow_reports_and_retries():
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 100., 100., 150., 100., 300, 200)
+    recs = _synthetic_records(7, 3000, [cam], (16, 16))
+    frame = R.Frame([cam])
+    proj = records_to_gpu(recs)
+    _, vals, _ = _oracle_bins(recs, frame)
+    bins = R.alloc_bins(frame, proj.mean2d.shape[0], capacity=len(vals) // 2)
+    R.bin_sort_into(proj, frame, bins)
+    torch.cuda.synchronize()
+    assert int(bins.error.item()) == 2                # GS_ERR_CAPACITY
+    assert int(bins.count.item()) == len(vals)        # the required size is reported
+    assert np.all(bins.ranges.cpu().numpy() == 0)     # and every list is empty
+    # the binding grows the buffer and redoes the sort
+    _check(recs, [cam], (16, 16), capacity=len(vals) // 2)
+
+
+def test_bin_sort_full_size_orbit_scene():
+    sc = scene("orbit")                       # 1.5M Gaussians, 1246x826, 16x16 tiles
+    cam = sc.cameras[0]
+    rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam)
+    M = _check([rec], [cam], (16, 16))
+    assert M > 1_000_000

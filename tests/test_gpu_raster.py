@@ -1,0 +1,139 @@
+"""gs_raster_fwd / gs_raster_bwd against the FP64 oracle on identical FP32 records.
+
+The oracle projects in FP64; its records rounded to FP32 are the input of both the
+CUDA path (gs_bin_sort + gs_raster_*) and the oracle compositing (evaluated in FP64).
+Pixels where a cut-off decision (alpha vs 1/255, T vs 1e-4) lies within rounding
+distance of its threshold are flagged by the oracle and excluded from the 1e-4
+bound; their number is asserted to be tiny and their error bounded.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import raster as oras
+from paper_2507_20239_gb300 import rasterizer as R
+from tests.gs_fixtures import oracle_lists, oracle_records_fp32, records_to_gpu, rel_l2, scene
+
+pytestmark = pytest.mark.gpu
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _oracle_fwd(rec, cam, tile, bg, tiles=None, d_image=None):
+    lists = oracle_lists(rec)
+    if d_image is None:
+        rt = oras.records_to_torch(rec["mean2d"], rec["conic"], rec["opacity"], rec["rgb"])
+        with torch.no_grad():
+            return oras.rasterize(rt, lists, cam.width, cam.height, tile[0], tile[1], bg, tiles), None
+    return oras.raster_vjp(rec["mean2d"], rec["conic"], rec["opacity"], rec["rgb"], lists, cam.width,
+                           cam.height, d_image, tile[0], tile[1], bg, tiles)
+
+
+def _gpu(recs, cams, tile, bg, store_stop=True):
+    frame = R.Frame(cams, tile=tile)
+    proj = records_to_gpu(recs)
+    bins = R.bin_sort(proj, frame)
+    img, T, stop = R.raster_fwd(proj, bins, frame, bg, store_stop=store_stop)
+    torch.cuda.synchronize()
+    return frame, proj, bins, img, T, stop
+
+
+def _tile_mask(cam, tile, tiles):
+    gx = (cam.width + tile[0] - 1) // tile[0]
+    m = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        tx, ty = t % gx, t // gx
+        m[ty * tile[1]:(ty + 1) * tile[1], tx * tile[0]:(tx + 1) * tile[0]] = True
+    return m
+
+
+def _compare_fwd(o, img, T, stop, mask=None):
+    flag = o["flag"]
+    sel = ~flag if mask is None else (~flag & mask)
+    err = np.abs(img - o["image"]).max(0)
+    assert err[sel].max() < IMG_TOL, err[sel].max()
+    assert np.abs(T - o["T_final"])[sel].max() < IMG_TOL
+    assert np.array_equal(stop[sel], o["stop"][sel])
+    tot = flag.sum() if mask is None else (flag & mask).sum()
+    assert tot <= max(2, 1e-3 * sel.sum()), tot
+    if tot:
+        assert err[flag if mask is None else flag & mask].max() < 1 / 255 + 1e-3
+    return tot
+
+
+@pytest.mark.parametrize("name,tile,bg", [("small", (16, 16), (0, 0, 0)), ("small", (8, 8), (0.2, 0.5, 1.0)),
+                                          ("orbit_small", (16, 16), (0, 0, 0)),
+                                          ("orbit_small", (16, 32), (0.3, 0.1, 0.7))])
+def test_raster_fwd_matches_oracle(name, tile, bg):
+    sc = scene(name)
+    cam = sc.cameras[0]
+    rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam, tile)
+    frame, proj, bins, img, T, stop = _gpu([rec], [cam], tile, bg)
+    o, _ = _oracle_fwd(rec, cam, tile, bg)
+    _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
+                 frame.view_pixels(stop, 0).cpu().numpy())
+
+
+def test_raster_fwd_ragged_image_and_empty_tiles():
+    # a 37x23 image (ragged last tile row/column) where most tiles are empty
+    from paper_2507_20239_gb300 import synth
+    sc = synth.small_scene(3, n=40, width=37, height=23)
+    cam = sc.cameras[0]
+    rec = oracle_records_fp32(sc.params(), 0, cam)
+    frame, proj, bins, img, T, stop = _gpu([rec], [cam], (16, 16), (0.1, 0.1, 0.1))
+    o, _ = _oracle_fwd(rec, cam, (16, 16), (0.1, 0.1, 0.1))
+    _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
+                 frame.view_pixels(stop, 0).cpu().numpy())
+
+
+@pytest.mark.parametrize("name,tile,bg", [("small", (16, 16), (0, 0, 0)), ("small", (8, 8), (0.2, 0.5, 1.0)),
+                                          ("orbit_small", (16, 16), (0.1, 0.2, 0.3))])
+def test_raster_bwd_matches_oracle(name, tile, bg):
+    sc = scene(name)
+    cam = sc.cameras[0]
+    rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam, tile)
+    frame, proj, bins, img, T, stop = _gpu([rec], [cam], tile, bg)
+    rng = np.random.default_rng(7)
+    d_image = rng.normal(0, 1, (3, cam.height, cam.width)).astype(np.float32)
+    o, g = _oracle_fwd(rec, cam, tile, bg, d_image=d_image)
+    assert o["flag"].sum() <= max(2, 1e-3 * o["flag"].size)
+    dg = torch.as_tensor(d_image.reshape(-1)).cuda()
+    rg = R.raster_bwd(proj, bins, frame, img, dg, bg)
+    torch.cuda.synchronize()
+    got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
+               d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
+    assert np.all(rg.d_rgb[:, 3].cpu().numpy() == 0)
+    for k in got:
+        e = rel_l2(got[k], g[k])
+        assert e < GRAD_TOL, (k, e)
+    # culled records receive nothing
+    cul = rec["radius"] == 0
+    assert np.all(got["d_mean2d"][cul] == 0)
+
+
+def test_raster_full_size_sampled_tiles():
+    """1.5M Gaussians at 1246x826 in the benchmark's launch configuration; the
+    oracle composites 24 sampled tiles (plus the 4 longest lists) and back-propagates
+    a d_image that is zero outside them."""
+    sc = scene("orbit")
+    cam = sc.cameras[0]
+    tile = (16, 16)
+    rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam, tile)
+    frame, proj, bins, img, T, stop = _gpu([rec], [cam], tile, (0, 0, 0))
+    ranges = bins.ranges.cpu().numpy()
+    lens = ranges[:, 1] - ranges[:, 0]
+    rng = np.random.default_rng(11)
+    busy = np.nonzero(lens > 0)[0]
+    tiles = sorted(set(rng.choice(busy, 24, replace=False).tolist()) | set(np.argsort(lens)[-4:].tolist()))
+    mask = _tile_mask(cam, tile, tiles)
+    d_image = np.where(mask[None], rng.normal(0, 1, (3, cam.height, cam.width)), 0).astype(np.float32)
+    o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
+    _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask)
+    rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda())
+    torch.cuda.synchronize()
+    got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
+               d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
+    for k in got:
+        e = rel_l2(got[k], g[k])
+        assert e < GRAD_TOL, (k, e)
