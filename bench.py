@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-tiles", type=int, default=48)
     ap.add_argument("--n", type=int, default=1_500_000)
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only (no e2e, batched or CPU legs): for profiler runs")
     return ap.parse_args()
 
 
@@ -239,6 +241,9 @@ def bench_ours(args, rank, local_rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
+    if args.quick:
+        print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "stages": stage_ms, "M": M}), flush=True)
+        return None
     # ---- end to end: camera + target H2D from pinned memory, loss D2H, every step
     tgt_host = step.target.cpu().pin_memory()
     cam_host = step.frame.cams_dev.cpu().pin_memory()
@@ -480,7 +485,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     out = bench_ours(args, rank, local_rank, world)
-    if rank == 0:
+    if out is not None and rank == 0:
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(make_scene(args.n, 0), args.cpu_sample_tiles)
         print(json.dumps(out), flush=True)

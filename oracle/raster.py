@@ -85,7 +85,7 @@ def tile_lists(rect, depth_f32, grid_x, grid_y):
 # ----------------------------------------------------------------------------------------
 # compositing (FP64, differentiable)
 # ----------------------------------------------------------------------------------------
-def composite(px, py, xy, conic, opacity, rgb, bg, flag_tol_alpha=1e-3, flag_tol_T=1e-3):
+def composite(px, py, xy, conic, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_tol_T=1e-3):
     """Eq. 2 for P pixels over one depth-ordered list of L Gaussians.
 
     px, py: [P] float64 sample coordinates; xy [L,2], conic [L,3], opacity [L],

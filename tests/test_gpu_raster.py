@@ -47,18 +47,24 @@ def _tile_mask(cam, tile, tiles):
     return m
 
 
-def _compare_fwd(o, img, T, stop, mask=None):
+def _compare_fwd(o, img, T, stop, mask=None, counts=None):
+    """Image and T within 1e-4, stop index and per-pixel work counts exact, on every
+    pixel the oracle does not flag; flagged pixels (a cut-off decision within the
+    FP32 error bound of its threshold) must be rare and within 1/255 + 1e-4."""
     flag = o["flag"]
     sel = ~flag if mask is None else (~flag & mask)
     err = np.abs(img - o["image"]).max(0)
     assert err[sel].max() < IMG_TOL, err[sel].max()
     assert np.abs(T - o["T_final"])[sel].max() < IMG_TOL
     assert np.array_equal(stop[sel], o["stop"][sel])
-    tot = flag.sum() if mask is None else (flag & mask).sum()
-    assert tot <= max(2, 1e-3 * sel.sum()), tot
-    if tot:
-        assert err[flag if mask is None else flag & mask].max() < 1 / 255 + 1e-3
-    return tot
+    if counts is not None:
+        assert np.array_equal(counts[..., 0][sel], o["n_examined"][sel])
+        assert np.array_equal(counts[..., 1][sel], o["n_contrib"][sel])
+    fl = flag if mask is None else (flag & mask)
+    assert fl.sum() <= max(2, 1e-2 * (sel.sum() + fl.sum())), fl.sum()
+    if fl.sum():
+        assert err[fl].max() < 1 / 255 + IMG_TOL
+    return int(fl.sum())
 
 
 @pytest.mark.parametrize("name,tile,bg", [("small", (16, 16), (0, 0, 0)), ("small", (8, 8), (0.2, 0.5, 1.0)),
@@ -70,8 +76,9 @@ def test_raster_fwd_matches_oracle(name, tile, bg):
     rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam, tile)
     frame, proj, bins, img, T, stop = _gpu([rec], [cam], tile, bg)
     o, _ = _oracle_fwd(rec, cam, tile, bg)
+    counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
-                 frame.view_pixels(stop, 0).cpu().numpy())
+                 frame.view_pixels(stop, 0).cpu().numpy(), counts=counts)
 
 
 def test_raster_fwd_ragged_image_and_empty_tiles():
@@ -96,7 +103,7 @@ def test_raster_bwd_matches_oracle(name, tile, bg):
     rng = np.random.default_rng(7)
     d_image = rng.normal(0, 1, (3, cam.height, cam.width)).astype(np.float32)
     o, g = _oracle_fwd(rec, cam, tile, bg, d_image=d_image)
-    assert o["flag"].sum() <= max(2, 1e-3 * o["flag"].size)
+    assert o["flag"].sum() <= max(2, 1e-2 * o["flag"].size)
     dg = torch.as_tensor(d_image.reshape(-1)).cuda()
     rg = R.raster_bwd(proj, bins, frame, img, dg, bg)
     torch.cuda.synchronize()
@@ -128,8 +135,9 @@ def test_raster_full_size_sampled_tiles():
     mask = _tile_mask(cam, tile, tiles)
     d_image = np.where(mask[None], rng.normal(0, 1, (3, cam.height, cam.width)), 0).astype(np.float32)
     o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
+    counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
-                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask)
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts)
     rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda())
     torch.cuda.synchronize()
     got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
