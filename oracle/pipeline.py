@@ -21,20 +21,26 @@ PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 def project_vjp(params: dict, sh_degree: int, cams: list, rec_grads: list, tile_w=16, tile_h=16):
     """Gradients of sum_v <records_v, rec_grads_v> w.r.t. the parameters.
 
-    rec_grads[v] is a dict d_mean2d [N,2], d_conic [N,3], d_opacity [N], d_rgb [N,3]
-    for view v; the parameter gradients are summed over views. Also returns the
+    rec_grads[v] is a dict d_mean2d [N,2], d_conic [N,3] (w.r.t. the factored conic
+    (A, beta, gamma)), d_opacity [N], d_rgb [N,3] for view v; the parameter gradients are summed over views. Also returns the
     per-view NDC-space mean2D gradients (d_u W/2, d_v H/2)."""
     p = params_to_torch(params, requires_grad=True)
     outs, grads = [], []
     for cam, g in zip(cams, rec_grads):
         pr = project(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
                      sh_degree, cam, tile_w, tile_h)
-        outs += [pr["mean2d"], pr["conic"], pr["opacity"], pr["rgb"]]
+        outs += [pr["mean2d"], pr["conic_f"], pr["opacity"], pr["rgb"]]
         grads += [torch.as_tensor(np.asarray(g[k], np.float64))
                   for k in ("d_mean2d", "d_conic", "d_opacity", "d_rgb")]
     torch.autograd.backward(outs, grads)
     return {k: (p[k].grad.numpy() if p[k].grad is not None else np.zeros(p[k].shape))
             for k in PARAM_KEYS}
+
+
+def proj_record_arrays(proj: dict) -> dict:
+    """The arrays binning needs, in FP64 (depth keys are FP32 by definition)."""
+    return dict(mean2d=proj["mean2d"], conic_f=proj["conic_f"], q_max=proj["q_max"], rect=proj["rect"],
+                depth=proj["depth"].astype(np.float32))
 
 
 def render_view(params: dict, sh_degree: int, cam, target=None, tile_w=16, tile_h=16,
@@ -49,23 +55,21 @@ def render_view(params: dict, sh_degree: int, cam, target=None, tile_w=16, tile_
         pr = project(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
                      sh_degree, cam, tile_w, tile_h)
     proj = {k: (v.numpy() if isinstance(v, torch.Tensor) else v) for k, v in pr.items()}
-    gx, gy = proj["grid"]
-    depth32 = proj["depth"].astype(np.float32)
-    lists = tile_lists(proj["rect"], depth32, gx, gy)
+    lists = tile_lists(proj_record_arrays(proj), cam.width, cam.height, tile_w, tile_h)
     res = dict(proj=proj, lists=lists)
     if target is None and d_image is None:
-        rec = records_to_torch(proj["mean2d"], proj["conic"], proj["opacity"], proj["rgb"])
+        rec = records_to_torch(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"])
         with torch.no_grad():
             res["render"] = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles)
         return res
     if d_image is None:
         with torch.no_grad():
-            rec = records_to_torch(proj["mean2d"], proj["conic"], proj["opacity"], proj["rgb"])
+            rec = records_to_torch(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"])
             fwd = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles)
         loss, d_image = l1_loss_grad(fwd["image"], target)
         res["loss"] = loss
     res["d_image"] = d_image
-    out, g = raster_vjp(proj["mean2d"], proj["conic"], proj["opacity"], proj["rgb"], lists,
+    out, g = raster_vjp(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"], lists,
                         cam.width, cam.height, d_image, tile_w, tile_h, bg, tiles)
     res["render"] = out
     res["rec_grads"] = g

@@ -8,8 +8,17 @@ and the SH-evaluated colour c_i of Eq. 2. Readings where the paper is silent:
   * near-plane cull at t_z <= near (0.2);
   * J is evaluated at the camera-space mean with t_x/t_z, t_y/t_z clamped to
     +-1.3 * (W/2)/f_x, +-1.3 * (H/2)/f_y (no gradient through a clamped ratio);
-  * a 0.3 px^2 low-pass dilation on the diagonal of Sigma'; cull when det <= 0;
-  * extent r = ceil(3 sqrt(lambda_max)), lambda_max = m + sqrt(max(0.1, m^2 - det));
+  * a 0.3 px^2 low-pass dilation on the diagonal: Sigma'' = Sigma' + 0.3 I =
+    [[a, b], [b, c]]; cull when det = ac - b^2 <= 0;
+  * the exponent of Eq. 1 in screen space, -1/2 d^T Sigma''^-1 d, is carried in
+    the factored form -1/2 (A (dx + beta dy)^2 + gamma dy^2) with A = c/det,
+    beta = -b/c, gamma = 1/c (an exact re-parametrisation of the conic);
+  * footprint: alpha = min(0.99, o G) reaches the 1/255 floor only where
+    d^T Sigma''^-1 d <= q_max = 2 ln(255 o); Gaussians with o < 1/255 are culled; the
+    tile rectangle covers the axis-aligned box of that ellipse, half-extents
+    sqrt(q_max a), sqrt(q_max c) (enlarged by the binning margin), and "radius" is
+    the larger half-extent rounded up (the 3-sigma square box of the 3DGS lineage
+    is not used: it drops pixels the alpha floor keeps and keeps tiles it drops);
   * mean2D u = f_x t_x / t_z + c_x (pixel (i, j) covers [i, i+1) x [j, j+1));
   * colour = sum_k sh_k Y_k(dir) + 0.5 per channel, clamped at 0, with dir the
     unit vector from the camera centre to the mean.
@@ -26,7 +35,11 @@ from .sh import sh_basis, num_coeffs
 NEAR = 0.2
 DILATION = 0.3
 FOV_CLAMP = 1.3
-EXTENT_SIGMAS = 3.0
+ALPHA_MIN = 1.0 / 255.0
+# Tiles are kept when their pixel-centre box meets the ellipse q <= q_max scaled by
+# this factor: a margin that keeps the tile test conservative against the per-pixel
+# alpha test's rounding.
+BIN_MARGIN = 1.002
 
 
 def quat_to_rotmat(q: torch.Tensor) -> torch.Tensor:
@@ -51,28 +64,67 @@ def tile_grid(width: int, height: int, tile_w: int, tile_h: int):
     return (width + tile_w - 1) // tile_w, (height + tile_h - 1) // tile_h
 
 
-def tile_rect(mean2d: np.ndarray, radius: np.ndarray, tile_w: int, tile_h: int,
+def tile_rect(mean2d: np.ndarray, half: np.ndarray, tile_w: int, tile_h: int,
               grid_x: int, grid_y: int) -> np.ndarray:
-    """Tile rectangle [x0, y0, x1, y1) of each record; all-zero for radius 0.
+    """Tile rectangle [x0, y0, x1, y1) covering the box mean2d +- half (half [N,2]).
 
-    x0 = clamp(floor((u - r) / tw), 0, gx), x1 = clamp(floor((u + (r + tw - 1)) / tw), 0, gx),
-    likewise for y. The arithmetic runs in mean2d's own dtype (FP32 for FP32
-    records): each of the subtraction/addition and the division is one rounded
-    operation of that precision, r and r + tw - 1 being exact integers.
+    x0 = clamp(floor((u - hx) / tw), 0, gx), x1 = clamp(floor((u + hx) / tw) + 1, 0, gx),
+    likewise for y, evaluated in mean2d's own dtype (each subtraction/addition and
+    division one rounded operation of that precision). Rows with a negative
+    half-extent are empty.
     """
     dt = mean2d.dtype.type
-    u = mean2d[:, 0]
-    v = mean2d[:, 1]
-    r = radius.astype(mean2d.dtype)
+    u, v = mean2d[:, 0], mean2d[:, 1]
+    hx, hy = half[:, 0].astype(mean2d.dtype), half[:, 1].astype(mean2d.dtype)
     tw, th = dt(tile_w), dt(tile_h)
-    x0 = np.floor((u - r) / tw)
-    y0 = np.floor((v - r) / th)
-    x1 = np.floor((u + (radius + (tile_w - 1)).astype(mean2d.dtype)) / tw)
-    y1 = np.floor((v + (radius + (tile_h - 1)).astype(mean2d.dtype)) / th)
+    x0 = np.floor((u - hx) / tw)
+    y0 = np.floor((v - hy) / th)
+    x1 = np.floor((u + hx) / tw) + 1
+    y1 = np.floor((v + hy) / th) + 1
     rect = np.stack([np.clip(x0, 0, grid_x), np.clip(y0, 0, grid_y),
                      np.clip(x1, 0, grid_x), np.clip(y1, 0, grid_y)], 1).astype(np.int64)
-    rect[radius <= 0] = 0
+    rect[(half[:, 0] < 0) | (half[:, 1] < 0)] = 0
     return rect
+
+
+def footprint_half(conic_f: np.ndarray, q_max: np.ndarray) -> np.ndarray:
+    """Half-extents (sqrt(qb Sigma''_xx), sqrt(qb Sigma''_yy)) of the footprint ellipse
+    from the factored conic: Sigma''_xx = 1/A + beta^2/gamma, Sigma''_yy = 1/gamma."""
+    A, b, g = conic_f[:, 0], conic_f[:, 1], conic_f[:, 2]
+    qb = q_max * BIN_MARGIN
+    return np.stack([np.sqrt(qb * (1.0 / A + b * b / g)), np.sqrt(qb / g)], 1)
+
+
+def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
+    """True where the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb, d = mean - p,
+    meets the box of pixel centres p in [X0, X1] x [Y0, Y1].
+
+    Elementwise over arrays of one dtype; every operation is a single rounded
+    operation of that dtype (the decision is taken in the precision of the data).
+    If the unconstrained minimum d = 0 lies in the box the test passes; otherwise
+    the minimum of the convex quadratic lies on an edge, at the clamped 1-D
+    minimiser (dx* = -beta dy on a fixed-dy edge, dy* = -(A beta dx)/(A beta^2 + gamma)
+    on a fixed-dx edge).
+    """
+    dxl, dxh = u - X1, u - X0
+    dyl, dyh = v - Y1, v - Y0
+    inside = (dxl <= 0) & (dxh >= 0) & (dyl <= 0) & (dyh >= 0)
+
+    def q(dx, dy):
+        t = dx + beta * dy
+        return A * (t * t) + gamma * (dy * dy)
+
+    ab = A * beta
+    den = ab * beta + gamma
+    m = None
+    for f in (dyl, dyh):
+        dx = np.minimum(np.maximum(-(beta * f), dxl), dxh)
+        c = q(dx, f)
+        m = c if m is None else np.minimum(m, c)
+    for e in (dxl, dxh):
+        dy = np.minimum(np.maximum(-((ab * e) / den), dyl), dyh)
+        m = np.minimum(m, q(e, dy))
+    return inside | (m <= qb)
 
 
 def camera_tensors(cam):
@@ -87,10 +139,11 @@ def project(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
 
     Inputs are torch float64 tensors (they may require grad): means [N,3],
     log_scales [N,3], quats [N,4], opacity_logits [N], sh [N,K,3]. Returns a
-    dict: mean2d [N,2], conic [N,3] = (A, B, C) of Sigma'^-1 (power =
-    -1/2 (A dx^2 + C dy^2) - B dx dy), depth [N], opacity [N], rgb [N,3],
+    dict: mean2d [N,2], conic [N,3] = (A, B, C) of Sigma''^-1 (power =
+    -1/2 (A dx^2 + C dy^2) - B dx dy), conic_f [N,3] = (A, beta, gamma), the same
+    conic factored, q_max [N] = 2 ln(255 o), depth [N], opacity [N], rgb [N,3],
     radius [N] int64 (0 = culled), rect [N,4] int64, visible [N] bool,
-    clamped [N,3] bool, and the diagnostics extent (3 sqrt(lambda_max)).
+    clamped [N,3] bool, and diagnostics (half-extents, det, cov2d = Sigma').
     Culled records carry zero gradient (their outputs are masked).
     """
     R, t = camera_tensors(cam)
@@ -119,18 +172,26 @@ def project(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
     ok = in_front & (det > 0).detach()
     det_safe = torch.where(ok, det, torch.ones_like(det))
     conic = torch.stack([c / det_safe, -b / det_safe, a / det_safe], -1)
-    mid = 0.5 * (a + c)
-    lam = mid + torch.sqrt(torch.clamp(mid * mid - det, min=0.1))
-    extent = EXTENT_SIGMAS * torch.sqrt(lam)
-    radius = torch.where(ok, torch.ceil(extent.detach()), torch.zeros_like(extent)).to(torch.int64)
+    c_safe = torch.where(ok, c, torch.ones_like(c))
+    conic_f = torch.stack([c / det_safe, -b / c_safe, 1.0 / c_safe], -1)      # (A, beta, gamma)
+    opacity = torch.sigmoid(opacity_logits)
+    o_np = opacity.detach().numpy()
+    ok = ok & torch.as_tensor(o_np >= ALPHA_MIN)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q_max = np.where(o_np >= ALPHA_MIN, 2.0 * np.log(255.0 * o_np), -1.0)
+        qb = q_max * BIN_MARGIN
+        hx = np.sqrt(qb * a.detach().numpy())
+        hy = np.sqrt(qb * c.detach().numpy())
+    half = np.where(ok.numpy()[:, None], np.stack([hx, hy], 1), -1.0)
     u = cam.fx * tcam[:, 0] / tz_safe + cam.cx
     v = cam.fy * tcam[:, 1] / tz_safe + cam.cy
     mean2d = torch.stack([u, v], -1)
     gx, gy = tile_grid(W, H, tile_w, tile_h)
-    rect = tile_rect(mean2d.detach().numpy(), radius.numpy(), tile_w, tile_h, gx, gy)
+    rect = tile_rect(mean2d.detach().numpy(), half, tile_w, tile_h, gx, gy)
     area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
     visible = torch.as_tensor(area > 0) & ok
-    radius = torch.where(visible, radius, torch.zeros_like(radius))
+    radius = torch.as_tensor(np.where(visible.numpy(), np.ceil(np.nan_to_num(np.maximum(hx, hy))), 0)
+                             .astype(np.int64))
     rect[~visible.numpy()] = 0
     # colour from SH, direction from the camera centre to the mean
     center = -(R.T @ t)
@@ -141,16 +202,17 @@ def project(means, log_scales, quats, opacity_logits, sh, sh_degree, cam,
     raw = torch.einsum("nk,nkc->nc", Y, sh[:, :K, :]) + 0.5
     clamped = (raw < 0).detach()
     rgb = torch.clamp(raw, min=0.0)
-    opacity = torch.sigmoid(opacity_logits)
     vis = visible[:, None]
     return dict(
         mean2d=torch.where(vis, mean2d, torch.zeros_like(mean2d)),
         conic=torch.where(vis, conic, torch.zeros_like(conic)),
+        conic_f=torch.where(vis, conic_f, torch.zeros_like(conic_f)),
+        q_max=np.where(visible.numpy(), q_max, 0.0),
         depth=torch.where(visible, tz, torch.zeros_like(tz)),
         opacity=torch.where(visible, opacity, torch.zeros_like(opacity)),
         rgb=torch.where(vis, rgb, torch.zeros_like(rgb)),
         radius=radius, rect=torch.as_tensor(rect), visible=visible, clamped=clamped & vis,
-        extent=extent.detach(), det=det.detach(), cov2d=cov2.detach(),
+        half=half, det=det.detach(), cov2d=cov2.detach(),
         n=n, grid=(gx, gy),
     )
 

@@ -13,15 +13,20 @@ list), with the rasterizer's cut-offs that the paper leaves implicit:
     transmittance T' = T (1 - sigma) fall below 1e-4 (that entry is excluded);
   * output = C + T_final * bg.
 
-N_p for a pixel is the tile's list: every visible record whose tile rectangle
-contains the tile, ordered by (FP32 depth bits, record index) -- "depth-sorted"
-and "tile-based" in the paper; the FP32 key is the precision of the stored depth.
+N_p for a pixel is the tile's list: every visible record whose footprint ellipse
+(the region where alpha can reach the 1/255 floor, with the binning margin) meets
+the tile's box of pixel centres, ordered by (FP32 depth bits, record index) --
+"depth-sorted" and "tile-based" in the paper; the FP32 key is the precision of the
+stored depth. Records carry the conic factored as (A, beta, gamma); the
+compositing expands it to (A, B, C) = (A, A beta, gamma + A beta^2).
 Gradients come from reverse-mode differentiation of this FP64 forward.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
+
+from .project import tile_hit, BIN_MARGIN
 
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
@@ -57,12 +62,36 @@ def depth_bits(depth_f32: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(depth_f32, dtype=np.float32).view(np.uint32)
 
 
-def bin_and_sort(rect, depth_f32, tile_offset, grid_x, n_tiles):
+def tile_filter(tile, rec, mean2d, conic_f, q_max, tile_offset, grid_x, widths, heights, tile_w, tile_h):
+    """Keep the (tile, record) candidates whose footprint ellipse meets the tile's
+    pixel-centre box; evaluated in the records' dtype (see project.tile_hit)."""
+    dt = mean2d.dtype.type
+    lt = tile - tile_offset[rec]
+    gx = grid_x[rec]
+    tx, ty = lt % gx, lt // gx
+    W, H = widths[rec], heights[rec]
+    X0 = (tx * tile_w).astype(mean2d.dtype) + dt(0.5)
+    X1 = np.minimum((tx + 1) * tile_w, W).astype(mean2d.dtype) - dt(0.5)
+    Y0 = (ty * tile_h).astype(mean2d.dtype) + dt(0.5)
+    Y1 = np.minimum((ty + 1) * tile_h, H).astype(mean2d.dtype) - dt(0.5)
+    qb = (q_max.astype(mean2d.dtype) * dt(BIN_MARGIN))[rec]
+    cf = conic_f.astype(mean2d.dtype)
+    hit = tile_hit(mean2d[rec, 0], mean2d[rec, 1], cf[rec, 0], cf[rec, 1], cf[rec, 2], qb, X0, X1, Y0, Y1)
+    return tile[hit], rec[hit]
+
+
+def bin_and_sort(rec_arrays: dict, tile_offset, grid_x, widths, heights, tile_w, tile_h, n_tiles):
     """Sorted duplicate list: keys = tile << 32 | depth bits, vals = record index,
     ordered by (tile, depth bits, record index); ranges[t] = [start, end) of tile
-    t in the sorted list (start = end for an empty tile)."""
-    tile, rec = emit_duplicates(rect, tile_offset, grid_x)
-    bits = depth_bits(depth_f32)[rec].astype(np.uint64)
+    t in the sorted list (start = end for an empty tile).
+
+    rec_arrays: mean2d [R,2], conic_f [R,3], q_max [R], rect [R,4], depth [R] (FP32
+    depth is the key); tile_offset, grid_x, widths, heights per record (its view).
+    """
+    tile, rec = emit_duplicates(rec_arrays["rect"], tile_offset, grid_x)
+    tile, rec = tile_filter(tile, rec, rec_arrays["mean2d"], rec_arrays["conic_f"], rec_arrays["q_max"],
+                            tile_offset, grid_x, widths, heights, tile_w, tile_h)
+    bits = depth_bits(rec_arrays["depth"])[rec].astype(np.uint64)
     order = np.lexsort((rec, bits, tile))
     tile_s = tile[order]
     keys = (tile_s.astype(np.uint64) << np.uint64(32)) | bits[order]
@@ -73,22 +102,25 @@ def bin_and_sort(rect, depth_f32, tile_offset, grid_x, n_tiles):
     return keys, vals, ranges
 
 
-def tile_lists(rect, depth_f32, grid_x, grid_y):
+def tile_lists(rec_arrays: dict, width, height, tile_w=16, tile_h=16):
     """Per-tile record lists of one view as a dict {tile: int64 array}."""
-    n = rect.shape[0]
-    off = np.zeros(n, np.int64)
-    gx = np.full(n, grid_x, np.int64)
-    _, vals, ranges = bin_and_sort(rect, depth_f32, off, gx, grid_x * grid_y)
-    return {t: vals[ranges[t, 0]:ranges[t, 1]].astype(np.int64) for t in range(grid_x * grid_y)}
+    n = rec_arrays["rect"].shape[0]
+    gx = (width + tile_w - 1) // tile_w
+    gy = (height + tile_h - 1) // tile_h
+    full = lambda x: np.full(n, x, np.int64)
+    _, vals, ranges = bin_and_sort(rec_arrays, full(0), full(gx), full(width), full(height), tile_w, tile_h,
+                                   gx * gy)
+    return {t: vals[ranges[t, 0]:ranges[t, 1]].astype(np.int64) for t in range(gx * gy)}
 
 
 # ----------------------------------------------------------------------------------------
 # compositing (FP64, differentiable)
 # ----------------------------------------------------------------------------------------
-def composite(px, py, xy, conic, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_tol_T=1e-3):
+def composite(px, py, xy, conic_f, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_tol_T=1e-3):
     """Eq. 2 for P pixels over one depth-ordered list of L Gaussians.
 
-    px, py: [P] float64 sample coordinates; xy [L,2], conic [L,3], opacity [L],
+    px, py: [P] float64 sample coordinates; xy [L,2], conic_f [L,3] = (A, beta,
+    gamma), opacity [L],
     rgb [L,3] torch float64 in list order; bg [3]. Returns (color [P,3], T_final [P],
     stop [P], n_examined [P], n_contrib [P], flag [P]); stop is one past the last
     contributing list position, n_examined counts list entries looked at up to and
@@ -106,7 +138,9 @@ def composite(px, py, xy, conic, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_tol
     pyt = torch.as_tensor(py, dtype=dt)[:, None]
     dx = xy[None, :, 0] - pxt                                   # [P,L]
     dy = xy[None, :, 1] - pyt
-    A, B, C = conic[None, :, 0], conic[None, :, 1], conic[None, :, 2]
+    A = conic_f[None, :, 0]
+    B = A * conic_f[None, :, 1]
+    C = conic_f[None, :, 2] + B * conic_f[None, :, 1]
     power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
     alpha = torch.clamp(opacity[None, :] * torch.exp(power), max=ALPHA_MAX)
     cand = ((power <= 0) & (alpha >= ALPHA_MIN)).detach()
@@ -152,7 +186,7 @@ def rasterize(rec, lists, width, height, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0
               tiles=None, d_image=None):
     """Render one view from projected records.
 
-    rec: dict of torch float64 tensors mean2d [N,2], conic [N,3], opacity [N],
+    rec: dict of torch float64 tensors mean2d [N,2], conic_f [N,3], opacity [N],
     rgb [N,3] (leaves that may require grad). lists: {tile: record indices in
     depth order} (see tile_lists). tiles: subset of tiles to render (default all).
     If d_image [3,H,W] is given, the vector-Jacobian product sum(image * d_image)
@@ -177,7 +211,7 @@ def rasterize(rec, lists, width, height, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0
             continue
         ids = torch.as_tensor(lists.get(t, np.zeros(0, np.int64)))
         out, Tf, st, ne, nc, fl = composite(
-            X + 0.5, Y + 0.5, rec["mean2d"][ids], rec["conic"][ids], rec["opacity"][ids],
+            X + 0.5, Y + 0.5, rec["mean2d"][ids], rec["conic_f"][ids], rec["opacity"][ids],
             rec["rgb"][ids], bg)
         if dimg is not None and ids.numel() > 0:
             g = dimg[:, Y, X].T                                   # [P,3]
@@ -194,21 +228,21 @@ def rasterize(rec, lists, width, height, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0
                 n_contrib=n_contrib, flag=flag)
 
 
-def records_to_torch(mean2d, conic, opacity, rgb, requires_grad=False):
+def records_to_torch(mean2d, conic_f, opacity, rgb, requires_grad=False):
     mk = lambda a: torch.tensor(np.asarray(a, np.float64), requires_grad=requires_grad)
-    return dict(mean2d=mk(mean2d), conic=mk(conic), opacity=mk(opacity), rgb=mk(rgb))
+    return dict(mean2d=mk(mean2d), conic_f=mk(conic_f), opacity=mk(opacity), rgb=mk(rgb))
 
 
-def raster_vjp(mean2d, conic, opacity, rgb, lists, width, height, d_image, tile_w=16,
+def raster_vjp(mean2d, conic_f, opacity, rgb, lists, width, height, d_image, tile_w=16,
                tile_h=16, bg=(0.0, 0.0, 0.0), tiles=None):
     """Gradients of sum(image * d_image) w.r.t. the projected records (FP64).
 
-    Returns (render dict, grads dict with d_mean2d [N,2], d_conic [N,3],
-    d_opacity [N], d_rgb [N,3])."""
-    rec = records_to_torch(mean2d, conic, opacity, rgb, requires_grad=True)
+    Returns (render dict, grads dict with d_mean2d [N,2], d_conic [N,3] (w.r.t.
+    (A, beta, gamma)), d_opacity [N], d_rgb [N,3])."""
+    rec = records_to_torch(mean2d, conic_f, opacity, rgb, requires_grad=True)
     out = rasterize(rec, lists, width, height, tile_w, tile_h, bg, tiles, d_image)
     g = {}
-    for k, name in (("mean2d", "d_mean2d"), ("conic", "d_conic"), ("opacity", "d_opacity"),
+    for k, name in (("mean2d", "d_mean2d"), ("conic_f", "d_conic"), ("opacity", "d_opacity"),
                     ("rgb", "d_rgb")):
         gr = rec[k].grad
         g[name] = np.zeros(rec[k].shape) if gr is None else gr.numpy()

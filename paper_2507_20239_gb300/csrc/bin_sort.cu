@@ -1,8 +1,11 @@
 // Tile binning and depth sort ("tile-based", "depth-sorted" rasterization, Sec.
 // "Preliminary" of the paper).
 //
-// Result: for every global tile, the visible records whose tile rectangle contains
-// it, ordered by (FP32 depth bits, record index), concatenated tile after tile.
+// Result: for every global tile, the visible records whose footprint ellipse (where
+// alpha can reach the 1/255 floor, with a 0.2% margin) meets the tile's box of pixel
+// centres, ordered by (FP32 depth bits, record index), concatenated tile after tile.
+// Candidate tiles are those under the footprint's bounding box (gs_project's rect);
+// the exact ellipse-box test (tile_hit) removes the rest.
 //
 // Instead of one wide radix sort on (tile << 32 | depth) keys over all duplicates,
 // the order is built in two stable stages that give the same permutation:
@@ -60,29 +63,54 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(const uint32_t *
   }
 }
 
-// Exclusive scan of hist[256 * G] in place (one block of 1024 threads).
+// Exclusive scan of the digit-major histogram hist[256][G] in place (one block of
+// 1024 threads): warp w owns digits w, w+32, ...; rows are read coalesced, digit
+// totals are scanned in shared memory, then each row is scanned with a carry.
 __global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t *hist, int G, const uint32_t *d_n,
                                                         const uint32_t *d_skip) {
   if (d_skip && *d_skip) return;
-  const uint32_t total = kRsBins * G;
-  const uint32_t per = (total + 1023) / 1024;
-  const uint32_t b = threadIdx.x * per, e = min(total, b + per);
-  uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += hist[i];
-  __shared__ uint32_t part[1024];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += y;
-    __syncthreads();
+  __shared__ uint32_t tot[kRsBins];
+  __shared__ uint32_t base[kRsBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = warp; d < kRsBins; d += 32) {
+    const uint32_t *row = hist + (size_t)d * G;
+    uint32_t s = 0;
+    for (int b = lane; b < G; b += 32) s += row[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) tot[d] = s;
   }
-  uint32_t run = part[threadIdx.x] - s;
-  for (uint32_t i = b; i < e; ++i) {
-    const uint32_t c = hist[i];
-    hist[i] = run;
-    run += c;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t carry = 0;
+    for (int c = 0; c < kRsBins; c += 32) {
+      const uint32_t x = tot[c + lane];
+      uint32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      base[c + lane] = carry + incl - x;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  __syncthreads();
+  for (int d = warp; d < kRsBins; d += 32) {
+    uint32_t *row = hist + (size_t)d * G;
+    uint32_t carry = base[d];
+    for (int b0 = 0; b0 < G; b0 += 32) {
+      const int b = b0 + lane;
+      const uint32_t x = b < G ? row[b] : 0u;
+      uint32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (b < G) row[b] = carry + incl - x;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
 }
 
@@ -183,24 +211,17 @@ struct VisibleCompact {
   __device__ void total(uint64_t t) const { *n_vis = (uint32_t)t; }
 };
 
-__device__ __forceinline__ uint32_t rect_area(const uint16_t *rect, uint32_t r) {
-  const uint2 q = reinterpret_cast<const uint2 *>(rect)[r];
-  const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
-  return (x1 - x0) * (y1 - y0);
-}
-
 struct TouchedOffsets {
-  const uint16_t *rect;
-  const uint32_t *order;      // records in depth order
+  const uint32_t *counts;     // tiles hit by each depth-ordered record
   const uint32_t *n_vis;
   uint32_t *offsets;
   uint64_t capacity;
-  uint32_t *m_total;          // M (clamped to 2^32-1)
+  uint32_t *m_total;          // M (0 on overflow)
   uint32_t *overflow;
   int64_t *d_count;
   int32_t *d_error;
   __device__ uint64_t count() const { return *n_vis; }
-  __device__ uint32_t value(uint64_t k) const { return rect_area(rect, order[k]); }
+  __device__ uint32_t value(uint64_t k) const { return counts[k]; }
   __device__ void emit(uint64_t k, uint64_t pre, uint32_t) const {
     if (pre <= 0xffffffffull) offsets[k] = (uint32_t)pre;
   }
@@ -213,28 +234,86 @@ struct TouchedOffsets {
   }
 };
 
-// One thread per depth-ordered record: write (tile id, record) for each tile of its rect.
-__global__ void emit_kernel(const uint16_t *__restrict__ rect, const uint32_t *__restrict__ order,
-                            const uint32_t *__restrict__ offsets, const uint32_t *n_vis, const uint32_t *overflow,
-                            const int32_t *__restrict__ view_of_record_tile_offset_unused,
-                            const gs_camera_t *__restrict__ cams, int n_views, int64_t n_per_view,
-                            uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
+struct RecordTiles {
+  uint32_t x0, y0, w, n;     // candidate rectangle (origin, width, count)
+  float u, v, A, beta, gamma, qb;
+  int W, H, toff, gx;
+};
+
+__device__ __forceinline__ RecordTiles record_tiles(const gs_proj_t &P, const gs_camera_t *cams, int n_views,
+                                                   int64_t n_per_view, uint32_t r) {
+  RecordTiles t;
+  const uint2 q = reinterpret_cast<const uint2 *>(P.rect)[r];
+  t.x0 = q.x & 0xffffu;
+  t.y0 = q.x >> 16;
+  t.w = (q.y & 0xffffu) - t.x0;
+  t.n = t.w * ((q.y >> 16) - t.y0);
+  const float2 m = reinterpret_cast<const float2 *>(P.mean2d)[r];
+  const float4 co = reinterpret_cast<const float4 *>(P.conic_opacity)[r];
+  t.u = m.x; t.v = m.y; t.A = co.x; t.beta = co.y; t.gamma = co.z;
+  t.qb = __fmul_rn(reinterpret_cast<const float4 *>(P.rgb)[r].w, kBinMargin);
+  const int view = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
+  t.W = cams[view].width; t.H = cams[view].height; t.toff = cams[view].tile_offset; t.gx = cams[view].grid_x;
+  return t;
+}
+
+// Candidate c of the record's rectangle: global tile id and whether the footprint
+// ellipse meets the tile's box of pixel centres.
+__device__ __forceinline__ bool candidate(const RecordTiles &t, uint32_t c, int tw, int th, uint32_t &tile) {
+  const uint32_t tx = t.x0 + c % t.w, ty = t.y0 + c / t.w;
+  tile = (uint32_t)t.toff + ty * (uint32_t)t.gx + tx;
+  const float X0 = (float)(tx * tw) + 0.5f, X1 = (float)min((int)(tx + 1) * tw, t.W) - 0.5f;
+  const float Y0 = (float)(ty * th) + 0.5f, Y1 = (float)min((int)(ty + 1) * th, t.H) - 0.5f;
+  return tile_hit(t.u, t.v, t.A, t.beta, t.gamma, t.qb, X0, X1, Y0, Y1);
+}
+
+// One warp per depth-ordered record: count the candidate tiles that pass.
+__global__ void tile_count_kernel(gs_proj_t P, const uint32_t *__restrict__ order, const uint32_t *n_vis,
+                                  const gs_camera_t *__restrict__ cams, int n_views, int64_t n_per_view, int tw,
+                                  int th, uint32_t *__restrict__ counts) {
+  const uint32_t nv = *n_vis;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nv; k += nw) {
+    const RecordTiles t = record_tiles(P, cams, n_views, n_per_view, order[k]);
+    uint32_t cnt = 0;
+    for (uint32_t base = 0; base < t.n; base += 32) {
+      const uint32_t c = base + lane;
+      uint32_t tile;
+      const bool hit = c < t.n && candidate(t, c, tw, th, tile);
+      cnt += __popc(__ballot_sync(0xffffffffu, hit));
+    }
+    if (lane == 0) counts[k] = cnt;
+  }
+}
+
+// One warp per depth-ordered record: write (tile id, record) for every passing tile,
+// in candidate order, at the record's offset.
+__global__ void emit_kernel(gs_proj_t P, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
+                            const uint32_t *n_vis, const uint32_t *overflow, const gs_camera_t *__restrict__ cams,
+                            int n_views, int64_t n_per_view, int tw, int th, uint32_t *__restrict__ dkeys,
+                            uint32_t *__restrict__ dvals) {
   if (*overflow) return;
   const uint32_t nv = *n_vis;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nv; k += nw) {
     const uint32_t r = order[k];
-    const uint2 q = reinterpret_cast<const uint2 *>(rect)[r];
-    const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
-    const int v = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
-    const uint32_t toff = (uint32_t)cams[v].tile_offset;
-    const uint32_t gx = (uint32_t)cams[v].grid_x;
+    const RecordTiles t = record_tiles(P, cams, n_views, n_per_view, r);
     uint32_t o = offsets[k];
-    for (uint32_t ty = y0; ty < y1; ++ty)
-      for (uint32_t tx = x0; tx < x1; ++tx) {
-        dkeys[o] = toff + ty * gx + tx;
-        dvals[o] = r;
-        ++o;
+    for (uint32_t base = 0; base < t.n; base += 32) {
+      const uint32_t c = base + lane;
+      uint32_t tile = 0;
+      const bool hit = c < t.n && candidate(t, c, tw, th, tile);
+      const uint32_t b = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const uint32_t pos = o + __popc(b & lt);
+        dkeys[pos] = tile;
+        dvals[pos] = r;
       }
+      o += __popc(b);
+    }
   }
 }
 
@@ -268,6 +347,7 @@ __global__ void keys64_kernel(const uint32_t *__restrict__ tiles, const uint32_t
 // ------------------------------------------------------------------ host side
 struct BinWs {
   uint32_t *vk0, *vv0, *vk1, *vv1;   // visible records: depth keys / record ids (double buffered)
+  uint32_t *counts;                  // tiles hit per depth-ordered record
   uint32_t *offsets;                 // duplicate offsets in depth order
   uint32_t *dk0, *dk1, *dv1;         // duplicate tile keys (double buffered) + second value buffer
   uint64_t *block_sums;
@@ -291,6 +371,7 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
   w.vv0 = (uint32_t *)take(4 * (size_t)R + 16);
   w.vk1 = (uint32_t *)take(4 * (size_t)R + 16);
   w.vv1 = (uint32_t *)take(4 * (size_t)R + 16);
+  w.counts = (uint32_t *)take(4 * (size_t)R + 16);
   w.offsets = (uint32_t *)take(4 * (size_t)R + 16);
   w.dk0 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
@@ -369,19 +450,22 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   bool in0 = true;
   if (gs_status_t st = radix_sort(w.vk0, w.vv0, w.vk1, w.vv1, n_vis, nullptr, 32, false, w.hist, G, s, &in0)) return st;
   const uint32_t *order = in0 ? w.vv0 : w.vv1;
-  // 3. duplicate offsets in depth order, M and the capacity check
-  TouchedOffsets to{proj->rect, order, n_vis, w.offsets, (uint64_t)bins->capacity, m_total, overflow,
-                    bins->d_count, d_error};
+  // 3. tiles hit per record, duplicate offsets in depth order, M and the capacity check
+  const int64_t n_per_view = R / frame->n_views;
+  const int eg = num_sms() * 8;
+  tile_count_kernel<<<eg, 256, 0, s>>>(*proj, order, n_vis, frame->cams_dev, frame->n_views, n_per_view,
+                                       frame->tile_w, frame->tile_h, w.counts);
+  GS_LAUNCH_CHECK();
+  TouchedOffsets to{w.counts, n_vis, w.offsets, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
   if (gs_status_t st = run_scan(to, w.block_sums, G, s)) return st;
   // 4. emit (tile, record) in depth order, into the buffer the tile sort ends in
   const int tile_bits = bits_for((uint32_t)(frame->n_tiles - 1));
   const int passes = (tile_bits + 7) / 8;
   uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
   const bool emit_to_A = (passes % 2) == 0;
-  const int64_t n_per_view = R / frame->n_views;
-  const int eg = num_sms() * 8;
-  emit_kernel<<<eg, 256, 0, s>>>(proj->rect, order, w.offsets, n_vis, overflow, nullptr, frame->cams_dev,
-                                 frame->n_views, n_per_view, emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
+  emit_kernel<<<eg, 256, 0, s>>>(*proj, order, w.offsets, n_vis, overflow, frame->cams_dev, frame->n_views,
+                                 n_per_view, frame->tile_w, frame->tile_h, emit_to_A ? A_k : B_k,
+                                 emit_to_A ? A_v : B_v);
   GS_LAUNCH_CHECK();
   // 5. stable sort by tile id
   bool res0 = true;

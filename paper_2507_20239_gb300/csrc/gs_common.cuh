@@ -55,25 +55,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Per-Gaussian form of the conic used by the rasterizer. With (A, B, C) the conic,
-// dx = u - p_x, dy = v - p_y:
-//   A dx^2 + 2 B dx dy + C dy^2 = A (dx + beta dy)^2 + gamma dy^2,
-//   beta = B / A, gamma = (A C - B^2) / A,
-// a sum of two non-negative terms: unlike the expanded form it does not cancel for
-// thin, elongated splats. A C - B^2 is computed with Kahan's FMA-compensated 2x2
-// determinant. Returns (A, beta, gamma, opacity).
-__device__ __forceinline__ float4 stage_conic(float4 co) {
-  const float A = co.x, B = co.y, C = co.z;
-  const float w = __fmul_rn(B, B);
-  const float e = __fmaf_rn(-B, B, w);   // w - B^2, exact
-  const float f = __fmaf_rn(A, C, -w);
-  const float det = __fadd_rn(f, e);
-  return make_float4(A, __fdiv_rn(B, A), __fdiv_rn(det, A), co.w);
-}
+constexpr float kBinMargin = 1.002f;    // tile test keeps q_min <= q_max * 1.002
 
-// Gaussian falloff term of Eq. 2 at one pixel, from the staged (A, beta, gamma, o).
-// Every rounding is explicit so that the forward and backward kernels take
-// identical skip / stop decisions.
+// Gaussian falloff term of Eq. 2 at one pixel. The conic is carried factored as
+// (A, beta, gamma): d^T Sigma''^-1 d = A (dx + beta dy)^2 + gamma dy^2, a sum of two
+// non-negative terms that does not cancel for thin, elongated splats. Every
+// rounding is explicit so that the forward and backward kernels take identical
+// skip / stop decisions.
 struct Falloff {
   float dx, dy, t, power, G, raw, alpha;
 };
@@ -90,6 +78,43 @@ __device__ __forceinline__ Falloff falloff(float u, float v, float A, float beta
   f.raw = __fmul_rn(o, f.G);
   f.alpha = fminf(kAlphaMax, f.raw);
   return f;
+}
+
+// Does the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb (d = mean - p) meet the box
+// of pixel centres p in [X0, X1] x [Y0, Y1]? Each operation is one IEEE FP32
+// rounding (no contraction), so the decision is reproducible op for op. If d = 0 is
+// inside the box the test passes; otherwise the minimum of the convex quadratic is
+// on an edge, at the clamped 1-D minimiser.
+__device__ __forceinline__ float qform_rn(float dx, float dy, float A, float beta, float gamma) {
+  const float t = __fadd_rn(dx, __fmul_rn(beta, dy));
+  return __fadd_rn(__fmul_rn(A, __fmul_rn(t, t)), __fmul_rn(gamma, __fmul_rn(dy, dy)));
+}
+
+__device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, float gamma, float qb, float X0,
+                                         float X1, float Y0, float Y1) {
+  const float dxl = __fsub_rn(u, X1), dxh = __fsub_rn(u, X0);
+  const float dyl = __fsub_rn(v, Y1), dyh = __fsub_rn(v, Y0);
+  if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return true;
+  const float ab = __fmul_rn(A, beta);
+  const float den = __fadd_rn(__fmul_rn(ab, beta), gamma);
+  float m;
+  {
+    const float dx = fminf(fmaxf(-__fmul_rn(beta, dyl), dxl), dxh);
+    m = qform_rn(dx, dyl, A, beta, gamma);
+  }
+  {
+    const float dx = fminf(fmaxf(-__fmul_rn(beta, dyh), dxl), dxh);
+    m = fminf(m, qform_rn(dx, dyh, A, beta, gamma));
+  }
+  {
+    const float dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(ab, dxl), den), dyl), dyh);
+    m = fminf(m, qform_rn(dxl, dy, A, beta, gamma));
+  }
+  {
+    const float dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(ab, dxh), den), dyl), dyh);
+    m = fminf(m, qform_rn(dxh, dy, A, beta, gamma));
+  }
+  return m <= qb;
 }
 
 // Find the view owning global tile t (views are few; a linear scan of the cameras).

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
     camera_space(cam, mx, my, mz, G.tx, G.ty, G.tz);
     bool ok = G.tz > cam.near_plane;
     int radius = 0, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-    float u = 0.f, vv = 0.f, A = 0.f, B = 0.f, C = 0.f;
+    float u = 0.f, vv = 0.f, A = 0.f, B = 0.f, C = 0.f, qmax = 0.f;   // (A, B, C) = (A, beta, gamma)
     if (ok) {
       const float4 q = reinterpret_cast<const float4 *>(P.quats)[g];
       const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
@@ -192,27 +192,28 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
       float M[9];
       scale_rot(Rq, s0, s1, s2, M);
       project_cov(cam, M, G);
-      ok = G.det > 0.f;
+      const float o_ = 1.f / (1.f + expf(-P.opacity_logits[g]));
+      ok = G.det > 0.f && o_ >= kAlphaMin;
       if (ok) {
-        const float idet = 1.f / G.det;
-        A = G.c * idet;
-        B = -G.b * idet;
-        C = G.a * idet;
-        // lambda_max = m + sqrt(max(0.1, m^2 - det)); m^2 - det = ((a-c)/2)^2 + b^2
-        const float mid = 0.5f * (G.a + G.c), hd = 0.5f * (G.a - G.c);
-        const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + G.b * G.b));
-        radius = (int)ceilf(3.f * sqrtf(lam));
+        // factored conic: A = c/det, beta = -b/c, gamma = 1/c
+        A = G.c / G.det;
+        B = -G.b / G.c;
+        C = 1.f / G.c;
+        // alpha = min(0.99, o G) reaches 1/255 only where d^T Sigma''^-1 d <= q_max
+        qmax = 2.f * logf(255.f * o_);
+        const float qb = __fmul_rn(qmax, kBinMargin);
+        const float hx = sqrtf(qb * G.a), hy = sqrtf(qb * G.c);
+        radius = (int)fminf(ceilf(fmaxf(hx, hy)), 1.0e9f);
         const float itz = 1.f / G.tz;
         u = cam.fx * G.tx * itz + cam.cx;
         vv = cam.fy * G.ty * itz + cam.cy;
-        // tile rectangle: one rounded FP32 add/sub and one division per bound
+        // tiles under the footprint's bounding box: one rounded FP32 add/sub and one
+        // division per bound
         const float ftw = (float)tile_w, fth = (float)tile_h;
-        x0 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(u, (float)radius), ftw)), 0.f), (float)cam.grid_x);
-        y0 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(vv, (float)radius), fth)), 0.f), (float)cam.grid_y);
-        x1 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fadd_rn(u, (float)(radius + tile_w - 1)), ftw)), 0.f),
-                        (float)cam.grid_x);
-        y1 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fadd_rn(vv, (float)(radius + tile_h - 1)), fth)), 0.f),
-                        (float)cam.grid_y);
+        x0 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(u, hx), ftw)), 0.f), (float)cam.grid_x);
+        y0 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fsub_rn(vv, hy), fth)), 0.f), (float)cam.grid_y);
+        x1 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fadd_rn(u, hx), ftw)) + 1.f, 0.f), (float)cam.grid_x);
+        y1 = (int)fminf(fmaxf(floorf(__fdiv_rn(__fadd_rn(vv, hy), fth)) + 1.f, 0.f), (float)cam.grid_y);
         ok = (x1 > x0) && (y1 > y0);
       }
     }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
     const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
     reinterpret_cast<float2 *>(out.mean2d)[r] = make_float2(u, vv);
     reinterpret_cast<float4 *>(out.conic_opacity)[r] = make_float4(A, B, C, o);
-    reinterpret_cast<float4 *>(out.rgb)[r] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cb, 0.f), 0.f);
+    reinterpret_cast<float4 *>(out.rgb)[r] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cb, 0.f), qmax);
     out.depth[r] = G.tz;
     out.radius[r] = radius;
     const uint32_t lo = (uint32_t)x0 | ((uint32_t)y0 << 16), hi = (uint32_t)x1 | ((uint32_t)y1 << 16);
@@ -303,12 +304,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
         acc = __fadd_rn(acc, __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy))));
         cnt += 1;
       }
-      // conic (A, B, C) = (c, -b, a) / det  ->  (a, b, c)
-      const float a = G.a, b = G.b, c = G.c;
-      const float id2 = 1.f / (G.det * G.det);
-      const float da = (-c * c * gco.x + b * c * gco.y - b * b * gco.z) * id2;
-      const float db = (2.f * b * c * gco.x - (a * c + b * b) * gco.y + 2.f * a * b * gco.z) * id2;
-      const float dc = (-b * b * gco.x + a * b * gco.y - a * a * gco.z) * id2;
+      // factored conic (A, beta, gamma) = (c/det, -b/c, 1/c)  ->  (a, b, c)
+      const float b = G.b, c = G.c;
+      const float id2 = 1.f / (G.det * G.det), ic = 1.f / c, ic2 = ic * ic;
+      const float da = -c * c * id2 * gco.x;
+      const float db = 2.f * b * c * id2 * gco.x - ic * gco.y;
+      const float dc = -b * b * id2 * gco.x + b * ic2 * gco.y - ic2 * gco.z;
       // a = |K0|^2 + 0.3, b = K0.K1, c = |K1|^2 + 0.3 with K = T M
       float dK0[3], dK1[3];
 #pragma unroll

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     if (base + t < n) {
       const uint32_t r = vals[rg.x + base + t];
       s_xy[t] = mean2d[r];
-      s_co[t] = stage_conic(conic_o[r]);
+      s_co[t] = conic_o[r];
       s_rgb[t] = rgb[r];
     }
     __syncthreads();
@@ -172,9 +172,8 @@ struct PixBwd {
 };
 
 // One pixel's contribution of the current Gaussian, accumulated into v[9] =
-// (d_u, d_v, d_A, d_B, d_C, d_o, d_r, d_g, d_b).
-// co = staged (A, beta, gamma, o); B = the conic's off-diagonal entry.
-__device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, const float4 co, float B,
+// (d_u, d_v, d_A, d_beta, d_gamma, d_o, d_r, d_g, d_b); co = (A, beta, gamma, o).
+__device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, const float4 co,
                                         const float4 c, float *v) {
   if (p.done) return false;
   const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, p.fx, fy);
@@ -195,12 +194,13 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, co
   v[8] = fmaf(p.d2, w, v[8]);
   if (f.raw <= kAlphaMax) {
     v[5] = fmaf(f.G, dLda, v[5]);
+    // P = -1/2 (A t^2 + gamma dy^2), t = dx + beta dy, dx = u - p_x, dy = v - p_y
     const float dP = dLda * f.raw;
-    // dP/du = -(A dx + B dy) = -A t, dP/dv = -(B dx + C dy) = -(B t + gamma dy)
-    v[0] -= dP * (co.x * f.t);
-    v[1] -= dP * fmaf(B, f.t, co.z * f.dy);
-    v[2] -= 0.5f * dP * f.dx * f.dx;
-    v[3] -= dP * f.dx * f.dy;
+    const float At = co.x * f.t;
+    v[0] -= dP * At;
+    v[1] -= dP * fmaf(At, co.y, co.z * f.dy);
+    v[2] -= 0.5f * dP * f.t * f.t;
+    v[3] -= dP * At * f.dy;
     v[4] -= 0.5f * dP * f.dy * f.dy;
   }
   return true;
@@ -217,7 +217,6 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
   __shared__ float4 s_co[NT];
   __shared__ float4 s_rgb[NT];
   __shared__ uint32_t s_rec[NT];
-  __shared__ float s_B[NT];
   __shared__ float s_acc[NT * 9];
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31;
@@ -248,9 +247,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
       const uint32_t r = vals[rg.x + base + t];
       s_rec[t] = r;
       s_xy[t] = mean2d[r];
-      const float4 co = conic_o[r];
-      s_co[t] = stage_conic(co);
-      s_B[t] = co.y;
+      s_co[t] = conic_o[r];
       s_rgb[t] = rgb[r];
     }
 #pragma unroll
@@ -261,10 +258,9 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
         const float2 xy = s_xy[j];
         const float4 co = s_co[j];
         const float4 c = s_rgb[j];
-        const float B = s_B[j];
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        bool any = pix_bwd(q0, fy, xy, co, B, c, v);
-        any |= pix_bwd(q1, fy, xy, co, B, c, v);
+        bool any = pix_bwd(q0, fy, xy, co, c, v);
+        any |= pix_bwd(q1, fy, xy, co, c, v);
         if (__any_sync(0xffffffffu, any)) warp_reduce9_add(v, s_acc + j * 9, lane);
       }
     }

@@ -23,15 +23,17 @@ def oracle_records_fp32(params: dict, sh_degree: int, cam, tile=(16, 16)) -> dic
     """FP64 oracle projection, rounded to FP32 records; rect decided in FP32 on them."""
     pr = oproj.project_np(params, sh_degree, cam, tile[0], tile[1])
     mean2d = pr["mean2d"].astype(np.float32)
-    radius = pr["radius"].astype(np.int32)
     gx, gy = pr["grid"]
-    rect = oproj.tile_rect(mean2d, radius, tile[0], tile[1], gx, gy)
+    half = pr["half"].astype(np.float32)
+    rect = oproj.tile_rect(mean2d, half, tile[0], tile[1], gx, gy)
     area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
-    radius = np.where(area > 0, radius, 0).astype(np.int32)
-    rect[area <= 0] = 0
-    return dict(mean2d=mean2d, conic=pr["conic"].astype(np.float32), opacity=pr["opacity"].astype(np.float32),
-                rgb=pr["rgb"].astype(np.float32), depth=pr["depth"].astype(np.float32), radius=radius, rect=rect,
-                grid=(gx, gy), proj64=pr)
+    vis = pr["visible"] & (area > 0)
+    rect[~vis] = 0
+    radius = np.where(vis, pr["radius"], 0).astype(np.int32)
+    return dict(mean2d=mean2d, conic_f=pr["conic_f"].astype(np.float32), opacity=pr["opacity"].astype(np.float32),
+                rgb=pr["rgb"].astype(np.float32), q_max=pr["q_max"].astype(np.float32),
+                depth=np.where(vis, pr["depth"], 0).astype(np.float32), radius=radius, rect=rect,
+                grid=(gx, gy), width=cam.width, height=cam.height, tile=tuple(tile), proj64=pr)
 
 
 def records_to_gpu(recs: list):
@@ -40,10 +42,11 @@ def records_to_gpu(recs: list):
     cat = lambda k: np.concatenate([r[k] for r in recs], 0)
     n = sum(r["mean2d"].shape[0] for r in recs)
     co = np.zeros((n, 4), np.float32)
-    co[:, :3] = cat("conic")
+    co[:, :3] = cat("conic_f")
     co[:, 3] = cat("opacity")
     rgb = np.zeros((n, 4), np.float32)
     rgb[:, :3] = cat("rgb")
+    rgb[:, 3] = cat("q_max")
     rect = cat("rect").astype(np.uint16).view(np.int16)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(DEV)
     return R.Projected(t(cat("mean2d")), t(co), t(rgb), t(cat("depth")), t(cat("radius").astype(np.int32)),
@@ -51,8 +54,7 @@ def records_to_gpu(recs: list):
 
 
 def oracle_lists(rec: dict):
-    gx, gy = rec["grid"]
-    return oras.tile_lists(rec["rect"], rec["depth"], gx, gy)
+    return oras.tile_lists(rec, rec["width"], rec["height"], *rec["tile"])
 
 
 def rel_l2(a, b):

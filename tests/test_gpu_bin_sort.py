@@ -15,26 +15,36 @@ pytestmark = pytest.mark.gpu
 
 def _synthetic_records(seed, n, cams, tile):
     recs = []
+    rng = np.random.default_rng(1000 + seed)
     for v, cam in enumerate(cams):
         m2, dep, rad = synth.random_records(seed + v, n, cam.width, cam.height)
+        sx = rng.uniform(0.6, 14, n)
+        sy = rng.uniform(0.6, 14, n)
+        conic_f = np.stack([1 / sx ** 2, rng.normal(0, 0.5, n), 1 / sy ** 2], 1).astype(np.float32)
+        o = rng.uniform(0.01, 0.99, n)
+        q_max = (2 * np.log(255 * o)).astype(np.float32)
+        half = oproj.footprint_half(conic_f.astype(np.float64), q_max.astype(np.float64)).astype(np.float32)
+        half[rad == 0] = -1
         gx, gy = oproj.tile_grid(cam.width, cam.height, *tile)
-        rect = oproj.tile_rect(m2, rad, tile[0], tile[1], gx, gy)
+        rect = oproj.tile_rect(m2, half, tile[0], tile[1], gx, gy)
         area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
-        rad = np.where(area > 0, rad, 0).astype(np.int32)
+        rad = np.where(area > 0, np.maximum(rad, 1), 0).astype(np.int32)
         rect[area <= 0] = 0
         z3 = np.zeros((n, 3), np.float32)
         recs.append(dict(mean2d=m2, depth=np.where(rad > 0, dep, 0).astype(np.float32), radius=rad, rect=rect,
-                         conic=z3, opacity=np.zeros(n, np.float32), rgb=z3, grid=(gx, gy)))
+                         conic_f=conic_f, q_max=q_max, opacity=o.astype(np.float32), rgb=z3, grid=(gx, gy),
+                         width=cam.width, height=cam.height, tile=tuple(tile)))
     return recs
 
 
 def _oracle_bins(recs, frame):
-    rect = np.concatenate([r["rect"] for r in recs])
-    depth = np.concatenate([r["depth"] for r in recs])
+    cat = lambda k: np.concatenate([r[k] for r in recs])
     n = recs[0]["rect"].shape[0]
-    toff = np.repeat([frame.views[v][3] for v in range(len(recs))], n).astype(np.int64)
-    gxs = np.repeat([frame.views[v][4] for v in range(len(recs))], n).astype(np.int64)
-    return oras.bin_and_sort(rect, depth, toff, gxs, frame.n_tiles)
+    V = len(recs)
+    arr = dict(mean2d=cat("mean2d"), conic_f=cat("conic_f"), q_max=cat("q_max"), rect=cat("rect"),
+               depth=cat("depth"))
+    per = lambda i: np.repeat([frame.views[v][i] for v in range(V)], n).astype(np.int64)
+    return oras.bin_and_sort(arr, per(3), per(4), per(0), per(1), frame.tile[0], frame.tile[1], frame.n_tiles)
 
 
 def _check(recs, cams, tile, capacity=None):
@@ -72,12 +82,19 @@ def test_bin_sort_edge_cases():
         recs[0][k][:] = 0
     recs[0]["rect"][:] = 0
     assert _check(recs, [cam], (16, 16)) == 0
-    # a single record, and all records at exactly the same depth (ties -> record order)
+    # a single record whose footprint covers all 6 tiles of its rectangle
     recs = _synthetic_records(4, 1, [cam], (16, 16))
     recs[0]["radius"][:] = 50
     recs[0]["rect"][0] = [0, 0, 3, 2]
     recs[0]["depth"][:] = 1.0
+    recs[0]["mean2d"][0] = [17.0, 9.0]
+    recs[0]["conic_f"][0] = [1e-4, 0.0, 1e-4]
     assert _check(recs, [cam], (16, 16)) == 6
+    # a thin diagonal footprint inside a large rectangle: only the tiles it crosses
+    recs[0]["conic_f"][0] = [1.0, -1.0, 1e-4]
+    recs[0]["q_max"][0] = 4.0
+    assert 0 < _check(recs, [cam], (16, 16)) < 6
+    # all records at exactly the same depth (ties -> record order)
     recs = _synthetic_records(5, 5000, [cam], (16, 16))
     recs[0]["depth"][recs[0]["radius"] > 0] = 2.5
     _check(recs, [cam], (16, 16))

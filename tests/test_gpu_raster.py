@@ -22,10 +22,10 @@ GRAD_TOL = 1e-3
 def _oracle_fwd(rec, cam, tile, bg, tiles=None, d_image=None):
     lists = oracle_lists(rec)
     if d_image is None:
-        rt = oras.records_to_torch(rec["mean2d"], rec["conic"], rec["opacity"], rec["rgb"])
+        rt = oras.records_to_torch(rec["mean2d"], rec["conic_f"], rec["opacity"], rec["rgb"])
         with torch.no_grad():
             return oras.rasterize(rt, lists, cam.width, cam.height, tile[0], tile[1], bg, tiles), None
-    return oras.raster_vjp(rec["mean2d"], rec["conic"], rec["opacity"], rec["rgb"], lists, cam.width,
+    return oras.raster_vjp(rec["mean2d"], rec["conic_f"], rec["opacity"], rec["rgb"], lists, cam.width,
                            cam.height, d_image, tile[0], tile[1], bg, tiles)
 
 

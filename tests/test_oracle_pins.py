@@ -117,8 +117,11 @@ def test_isotropic_on_axis_closed_form():
     assert np.allclose(out["conic"][0], [1 / s2, 0.0, 1 / s2], rtol=1e-13)
     assert np.allclose(out["mean2d"][0], [32.0, 32.0])
     assert out["depth"][0] == d
-    # lambda_max = m + sqrt(max(0.1, m^2 - det)) with m^2 - det = 0
-    assert out["radius"][0] == math.ceil(3 * math.sqrt(s2 + math.sqrt(0.1)))
+    assert np.allclose(out["conic_f"][0], [1 / s2, 0.0, 1 / s2], rtol=1e-13)
+    # alpha >= 1/255 inside the circle rho^2 <= s2 q_max, q_max = 2 ln(255 o), o = 1/2
+    q_max = 2 * math.log(255 * 0.5)
+    assert abs(out["q_max"][0] - q_max) < 1e-12
+    assert out["radius"][0] == math.ceil(math.sqrt(q_max * 1.002 * s2))
 
 
 def _pinhole(p, cam):
@@ -191,16 +194,17 @@ def test_sh_colour_direction_from_camera_centre():
     assert abs(out["rgb"][0][0] - (math.sqrt(3 / (4 * math.pi)) + 0.5)) < 1e-14
 
 
-def test_tile_rect_integer_means_brute_force():
+def test_tile_rect_integer_bounds_brute_force():
     rng = np.random.default_rng(5)
     tw, th, gx, gy = 16, 8, 5, 7
     u = rng.integers(-40, 120, 200).astype(np.float32)
     v = rng.integers(-40, 100, 200).astype(np.float32)
-    r = rng.integers(1, 30, 200).astype(np.int32)
-    rect = oproj.tile_rect(np.stack([u, v], 1), r, tw, th, gx, gy)
+    half = rng.integers(0, 30, (200, 2)).astype(np.float32)
+    rect = oproj.tile_rect(np.stack([u, v], 1), half, tw, th, gx, gy)
     for i in range(200):
-        xs = [tx for tx in range(gx) if tx * tw < u[i] + r[i] and (tx + 1) * tw > u[i] - r[i]]
-        ys = [ty for ty in range(gy) if ty * th < v[i] + r[i] and (ty + 1) * th > v[i] - r[i]]
+        # tiles whose pixel span [t*tw, (t+1)*tw) meets the closed box [u - hx, u + hx]
+        xs = [tx for tx in range(gx) if tx * tw <= u[i] + half[i, 0] and (tx + 1) * tw > u[i] - half[i, 0]]
+        ys = [ty for ty in range(gy) if ty * th <= v[i] + half[i, 1] and (ty + 1) * th > v[i] - half[i, 1]]
         want = (xs[0], ys[0], xs[-1] + 1, ys[-1] + 1) if xs and ys else None
         got = tuple(rect[i])
         if want is None:
@@ -209,7 +213,51 @@ def test_tile_rect_integer_means_brute_force():
             assert got == want, (i, got, want)
 
 
+def _rand_conic_f(rng, n, dtype=np.float64):
+    L = rng.uniform(0.5, 12, (n, 2))
+    th_ = rng.uniform(0, math.pi, n)
+    out = np.zeros((n, 3))
+    for g in range(n):
+        Rm = np.array([[math.cos(th_[g]), -math.sin(th_[g])], [math.sin(th_[g]), math.cos(th_[g])]])
+        Ci = np.linalg.inv(Rm @ np.diag(L[g] ** 2) @ Rm.T)
+        out[g] = [Ci[0, 0], Ci[0, 1] / Ci[0, 0], Ci[1, 1] - Ci[0, 1] ** 2 / Ci[0, 0]]
+    return out.astype(dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_tile_hit_matches_dense_sampling(dtype):
+    rng = np.random.default_rng(12)
+    n = 400
+    cf = _rand_conic_f(rng, n, dtype)
+    u = rng.uniform(-20, 50, n).astype(dtype)
+    v = rng.uniform(-20, 50, n).astype(dtype)
+    qb = rng.uniform(1, 12, n).astype(dtype)
+    X0, X1, Y0, Y1 = (np.full(n, x, dtype) for x in (8.5, 23.5, 16.5, 31.5))
+    hit = oproj.tile_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb, X0, X1, Y0, Y1)
+    g = np.linspace(0, 1, 61)
+    for i in range(n):
+        px = X0[i] + g * (X1[i] - X0[i])
+        py = Y0[i] + g * (Y1[i] - Y0[i])
+        PX, PY = np.meshgrid(px.astype(np.float64), py.astype(np.float64))
+        dx, dy = float(u[i]) - PX, float(v[i]) - PY
+        A, b, c = (float(x) for x in cf[i])
+        q = A * (dx + b * dy) ** 2 + c * dy ** 2
+        if q.min() <= float(qb[i]) * (1 - 1e-5):
+            assert hit[i], i                         # a sampled point inside: must hit
+        # the true box minimum lies within the grid spacing of a sample
+        step = np.hypot((X1[i] - X0[i]) / 60, (Y1[i] - Y0[i]) / 60)
+        if hit[i]:
+            grad = 2 * math.sqrt(max(A, c)) * math.sqrt(q.min()) * (1 + abs(b)) * step + 1e-6
+            assert q.min() <= float(qb[i]) * (1 + 1e-5) + grad, i
+
+
 # ------------------------------------------------------------------ binning and sorting
+def _all_pass_records(rect, depth, n):
+    """Records whose footprint covers every candidate tile (q_max huge)."""
+    return dict(mean2d=np.zeros((n, 2)), conic_f=np.tile([1e-6, 0.0, 1e-6], (n, 1)), q_max=np.full(n, 1e30),
+                rect=rect, depth=depth)
+
+
 def test_bin_and_sort_brute_force():
     rng = np.random.default_rng(6)
     n, gx, gy = 60, 4, 3
@@ -218,8 +266,9 @@ def test_bin_and_sort_brute_force():
         x0, y0 = rng.integers(0, gx), rng.integers(0, gy)
         rect[i] = [x0, y0, rng.integers(x0, gx + 1), rng.integers(y0, gy + 1)]
     depth = rng.choice(np.float32([0.5, 1.0, 1.5, 2.25]), n)     # many exact ties
-    keys, vals, ranges = oras.bin_and_sort(rect, depth, np.zeros(n, np.int64),
-                                           np.full(n, gx, np.int64), gx * gy)
+    full = lambda x: np.full(n, x, np.int64)
+    keys, vals, ranges = oras.bin_and_sort(_all_pass_records(rect, depth, n), full(0), full(gx), full(64),
+                                           full(48), 16, 16, gx * gy)
     pairs = []
     for i in range(n):
         for ty in range(rect[i, 1], rect[i, 3]):
@@ -236,18 +285,45 @@ def test_bin_and_sort_brute_force():
         assert tuple(ranges[t]) == (start, start + len(sel))
 
 
+def test_tight_lists_do_not_change_the_image():
+    # dropping (record, tile) pairs whose footprint misses the tile leaves Eq. 2 unchanged
+    sc = small_scene(1, n=300)
+    cam = sc.cameras[0]
+    res = opipe.render_view(sc.params(), 0, cam)
+    pr = res["proj"]
+    n = sc.n
+    loose = dict(opipe.proj_record_arrays(pr))
+    loose["q_max"] = np.where(pr["visible"], 1e30, 0.0)
+    lists_loose = oras.tile_lists(loose, cam.width, cam.height)
+    tight = sum(len(l) for l in res["lists"].values())
+    assert tight < sum(len(l) for l in lists_loose.values())
+    rec = oras.records_to_torch(pr["mean2d"], pr["conic_f"], pr["opacity"], pr["rgb"])
+    with torch.no_grad():
+        out = oras.rasterize(rec, lists_loose, cam.width, cam.height)
+    assert np.abs(out["image"] - res["render"]["image"]).max() < 1e-14
+    assert np.abs(out["T_final"] - res["render"]["T_final"]).max() < 1e-14
+
+
 # ------------------------------------------------------------------ compositing
 def _records(n):
     return dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n),
                 rgb=np.zeros((n, 3)))
 
 
+def _to_factored(conic):
+    conic = np.asarray(conic, np.float64)
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    return np.stack([A, B / A, C - B * B / A], 1)
+
+
 def _render(recs, W, H, depth, radius=20, tw=16, th=16, bg=(0, 0, 0)):
-    gx, gy = oproj.tile_grid(W, H, tw, th)
-    rect = oproj.tile_rect(recs["mean2d"].astype(np.float32),
-                           np.full(len(depth), radius, np.int32), tw, th, gx, gy)
-    lists = oras.tile_lists(rect, np.float32(depth), gx, gy)
-    rt = oras.records_to_torch(recs["mean2d"], recs["conic"], recs["opacity"], recs["rgb"])
+    n = len(depth)
+    rect = oproj.tile_rect(recs["mean2d"].astype(np.float32), np.full((n, 2), radius, np.float32), tw, th,
+                           *oproj.tile_grid(W, H, tw, th))
+    arr = dict(mean2d=recs["mean2d"], conic_f=_to_factored(recs["conic"]), q_max=np.full(n, 1e30), rect=rect,
+               depth=np.float32(depth))
+    lists = oras.tile_lists(arr, W, H, tw, th)
+    rt = oras.records_to_torch(recs["mean2d"], arr["conic_f"], recs["opacity"], recs["rgb"])
     with torch.no_grad():
         return oras.rasterize(rt, lists, W, H, tw, th, bg)
 
@@ -332,11 +408,11 @@ def test_compositing_matches_brute_force(seed):
     opacity = rng.uniform(0.3, 1.0, n)     # >= 0.99 clamp exercised
     rgb = rng.uniform(0, 1, (n, 3))
     depth = rng.choice(np.float32([1.0, 1.25, 2.0, 3.0, 3.5]), n)
-    radius = np.full(n, 12, np.int32)
     gx, gy = oproj.tile_grid(W, H, tw, th)
-    rect = oproj.tile_rect(mean2d.astype(np.float32), radius, tw, th, gx, gy)
-    lists = oras.tile_lists(rect, depth, gx, gy)
-    rt = oras.records_to_torch(mean2d, conic, opacity, rgb)
+    rect = oproj.tile_rect(mean2d.astype(np.float32), np.full((n, 2), 12, np.float32), tw, th, gx, gy)
+    arr = dict(mean2d=mean2d, conic_f=_to_factored(conic), q_max=np.full(n, 1e30), rect=rect, depth=depth)
+    lists = oras.tile_lists(arr, W, H, tw, th)
+    rt = oras.records_to_torch(mean2d, arr["conic_f"], opacity, rgb)
     bg = (0.1, 0.2, 0.3)
     with torch.no_grad():
         out = oras.rasterize(rt, lists, W, H, tw, th, bg)
@@ -370,7 +446,7 @@ def test_compositing_transmittance_non_increasing():
     rng = np.random.default_rng(7)
     L = 40
     xy = torch.tensor(rng.uniform(0, 16, (L, 2)))
-    conic = torch.tensor(np.tile([0.05, 0.0, 0.05], (L, 1)))
+    conic = torch.tensor(np.tile([0.05, 0.0, 0.05], (L, 1)))        # isotropic: (A, beta, gamma)
     op = torch.tensor(rng.uniform(0.2, 0.9, L))
     rgb = torch.tensor(rng.uniform(0, 1, (L, 3)))
     px = np.arange(16) + 0.5
@@ -599,9 +675,5 @@ def test_anisotropic_footprint_matches_inverse_covariance():
     d = np.stack([X - pr["mean2d"][0, 0], Y - pr["mean2d"][0, 1]], -1)
     q = np.einsum("hwi,ij,hwj->hw", d, Sinv, d)
     a = np.minimum(0.99, o * np.exp(-0.5 * q))
-    gx, gy = pr["grid"]
-    inside = np.zeros((32, 32), bool)
-    x0, y0, x1, y1 = pr["rect"][0]
-    inside[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
-    a = np.where((a >= 1 / 255) & inside, a, 0.0)
+    a = np.where(a >= 1 / 255, a, 0.0)                  # the tile lists lose no such pixel
     assert np.abs(res["render"]["image"][0] - c * a).max() < 1e-13
