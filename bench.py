@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-tiles", type=int, default=48)
     ap.add_argument("--n", type=int, default=1_500_000)
+    ap.add_argument("--tile", default="16x16", help="tile shape WxH (16x16, 8x8, 16x32, 32x16)")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no e2e, batched or CPU legs): for profiler runs")
     return ap.parse_args()
@@ -191,6 +192,7 @@ def measure_capacity(sc, frame, P):
     M = int(bins.count.item())
     counts = R.raster_count(proj, bins, frame)
     c = counts.double().sum(0).cpu().numpy()
+    measure_capacity.last_counts = counts
     return M, float(c[0]), float(c[1]), proj
 
 
@@ -203,7 +205,8 @@ def bench_ours(args, rank, local_rank, world):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     sc = make_scene(args.n, rank)
-    frame = R.Frame(sc.cameras, device=dev)
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    frame = R.Frame(sc.cameras, tile=tile, device=dev)
     P = R.to_device_params(sc.params(), dev)
     M, p_exam, p_contrib, _ = measure_capacity(sc, frame, P)
     step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
@@ -242,7 +245,9 @@ def bench_ours(args, rank, local_rank, world):
         ms = float(t.item())
 
     if args.quick:
-        print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "stages": stage_ms, "M": M}), flush=True)
+        print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "stages": stage_ms, "M": M,
+                          "pairs_examined": p_exam, "pairs_composited": p_contrib,
+                          "tile_sync": tile_sync_stats(frame, measure_capacity.last_counts)}), flush=True)
         return None
     # ---- end to end: camera + target H2D from pinned memory, loss D2H, every step
     tgt_host = step.target.cpu().pin_memory()
@@ -313,7 +318,7 @@ def bench_ours(args, rank, local_rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded surface-patch scene standing in for MipNeRF-360-scale captures)",
         "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_degree": sc.sh_degree,
-                   "width": sc.cameras[0].width, "height": sc.cameras[0].height, "tile": "16x16",
+                   "width": sc.cameras[0].width, "height": sc.cameras[0].height, "tile": args.tile,
                    "views_per_step": frame.n_views, "duplicates_M": M, "pairs_examined": p_exam,
                    "pairs_composited": p_contrib, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (354 MB parameters read per step)"},
@@ -328,6 +333,25 @@ def bench_ours(args, rank, local_rank, world):
     if rank == 0 and not args.no_batched:
         out["batched"] = bench_batched(args, dev)
     return out
+
+
+def tile_sync_stats(frame, counts):
+    """Entries a tile's CTA walks (its pixels' maximum examined count, for every
+    pixel) against the entries its pixels need (their own examined counts)."""
+    import torch
+    W, H = frame.views[0][:2]
+    tw, th = frame.tile
+    ex = counts[:, 0].view(H, W).double()
+    gx, gy = (W + tw - 1) // tw, (H + th - 1) // th
+    pad = torch.zeros(gy * th, gx * tw, dtype=torch.float64, device=ex.device)
+    pad[:H, :W] = ex
+    t = pad.view(gy, th, gx, tw).permute(0, 2, 1, 3).reshape(gy * gx, th * tw)
+    walked = float(t.max(1).values.sum() * th * tw)
+    need = float(ex.sum())
+    # the same at warp granularity (16 x 4 pixel strips of a 16x16 tile)
+    wv = pad.view(gy, th // 4, 4, gx, tw).permute(0, 3, 1, 2, 4).reshape(-1, 4 * tw)
+    walked_w = float(wv.max(1).values.sum() * 4 * tw)
+    return {"needed": need, "walked_tile": walked, "walked_warp": walked_w}
 
 
 def load_traffic(kernel):

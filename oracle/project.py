@@ -103,8 +103,9 @@ def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
     operation of that dtype (the decision is taken in the precision of the data).
     If the unconstrained minimum d = 0 lies in the box the test passes; otherwise
     the minimum of the convex quadratic lies on an edge, at the clamped 1-D
-    minimiser (dx* = -beta dy on a fixed-dy edge, dy* = -(A beta dx)/(A beta^2 + gamma)
-    on a fixed-dx edge).
+    minimiser (dx* = -beta dy on a fixed-dy edge, dy* = -(A beta dx) / (A beta^2 + gamma)
+    on a fixed-dx edge, evaluated as -((A beta) dx) (1 / (A beta^2 + gamma)) with the
+    reciprocal formed once per record).
     """
     dxl, dxh = u - X1, u - X0
     dyl, dyh = v - Y1, v - Y0
@@ -115,14 +116,14 @@ def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
         return A * (t * t) + gamma * (dy * dy)
 
     ab = A * beta
-    den = ab * beta + gamma
+    inv_den = (ab * beta + gamma).dtype.type(1) / (ab * beta + gamma)
     m = None
     for f in (dyl, dyh):
         dx = np.minimum(np.maximum(-(beta * f), dxl), dxh)
         c = q(dx, f)
         m = c if m is None else np.minimum(m, c)
     for e in (dxl, dxh):
-        dy = np.minimum(np.maximum(-((ab * e) / den), dyl), dyh)
+        dy = np.minimum(np.maximum(-((ab * e) * inv_den), dyl), dyh)
         m = np.minimum(m, q(e, dy))
     return inside | (m <= qb)
 

@@ -63,55 +63,29 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(const uint32_t *
   }
 }
 
-// Exclusive scan of the digit-major histogram hist[256][G] in place (one block of
-// 1024 threads): warp w owns digits w, w+32, ...; rows are read coalesced, digit
-// totals are scanned in shared memory, then each row is scanned with a carry.
-__global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t *hist, int G, const uint32_t *d_n,
-                                                        const uint32_t *d_skip) {
+// Per-digit exclusive scan of the digit-major histogram hist[256][G] over blocks,
+// in place: one warp per digit (grid of 256 warps), so every row is read and
+// written coalesced and all rows proceed in parallel; the digit total goes to
+// totals[d]. The digit bases (exclusive scan of totals) are added by the downsweep.
+__global__ void __launch_bounds__(32) rs_scan_kernel(uint32_t *hist, int G, uint32_t *totals,
+                                                      const uint32_t *d_skip) {
   if (d_skip && *d_skip) return;
-  __shared__ uint32_t tot[kRsBins];
-  __shared__ uint32_t base[kRsBins];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = warp; d < kRsBins; d += 32) {
-    const uint32_t *row = hist + (size_t)d * G;
-    uint32_t s = 0;
-    for (int b = lane; b < G; b += 32) s += row[b];
+  const int lane = threadIdx.x, d = blockIdx.x;
+  uint32_t *row = hist + (size_t)d * G;
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < G; b0 += 32) {
+    const int b = b0 + lane;
+    const uint32_t x = b < G ? row[b] : 0u;
+    uint32_t incl = x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) tot[d] = s;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t carry = 0;
-    for (int c = 0; c < kRsBins; c += 32) {
-      const uint32_t x = tot[c + lane];
-      uint32_t incl = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      base[c + lane] = carry + incl - x;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
+    if (b < G) row[b] = carry + incl - x;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  __syncthreads();
-  for (int d = warp; d < kRsBins; d += 32) {
-    uint32_t *row = hist + (size_t)d * G;
-    uint32_t carry = base[d];
-    for (int b0 = 0; b0 < G; b0 += 32) {
-      const int b = b0 + lane;
-      const uint32_t x = b < G ? row[b] : 0u;
-      uint32_t incl = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (b < G) row[b] = carry + incl - x;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-  }
+  if (lane == 0) totals[d] = carry;
 }
 
 // Stable scatter. Each warp ranks a contiguous 512-key slice of the tile, 32 keys per
@@ -120,7 +94,7 @@ __global__ void __launch_bounds__(1024) rs_scan_kernel(uint32_t *hist, int G, co
 __global__ void __launch_bounds__(kRsThreads) rs_downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *d_n, const uint32_t *d_skip, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist) {
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
   __shared__ uint32_t s_keys[kRsTile];
   __shared__ uint32_t s_vals[kRsTile];
   __shared__ uint32_t s_whist[kRsWarps][kRsBins + 1];
@@ -132,7 +106,12 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_kernel(
   chunk_of(n, G, kRsTile, begin, end);
   if (begin >= end) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kRsBins; d += kRsThreads) s_goff[d] = hist[(uint64_t)d * G + blockIdx.x];
+  {
+    // digit bases: exclusive scan of the digit totals, then this block's column
+    uint32_t all;
+    const uint32_t dbase = block_exclusive_scan<uint32_t>(totals[threadIdx.x], &all);
+    s_goff[threadIdx.x] = dbase + hist[(uint64_t)threadIdx.x * G + blockIdx.x];
+  }
   const uint32_t lt_mask = lanemask_lt();
   for (uint64_t tb = begin; tb < end; tb += kRsTile) {
     const uint32_t tile_n = (uint32_t)min((uint64_t)kRsTile, end - tb);
@@ -236,7 +215,7 @@ struct TouchedOffsets {
 
 struct RecordTiles {
   uint32_t x0, y0, w, n;     // candidate rectangle (origin, width, count)
-  float u, v, A, beta, gamma, qb;
+  float u, v, A, beta, gamma, qb, ab, inv_den;
   int W, H, toff, gx;
 };
 
@@ -246,12 +225,14 @@ __device__ __forceinline__ RecordTiles record_tiles(const gs_proj_t &P, const gs
   const uint2 q = reinterpret_cast<const uint2 *>(P.rect)[r];
   t.x0 = q.x & 0xffffu;
   t.y0 = q.x >> 16;
-  t.w = (q.y & 0xffffu) - t.x0;
-  t.n = t.w * ((q.y >> 16) - t.y0);
+  const uint32_t x1 = q.y & 0xffffu, y1 = q.y >> 16;
+  t.w = x1 > t.x0 ? x1 - t.x0 : 0u;
+  t.n = (x1 > t.x0 && y1 > t.y0) ? t.w * (y1 - t.y0) : 0u;
   const float2 m = reinterpret_cast<const float2 *>(P.mean2d)[r];
   const float4 co = reinterpret_cast<const float4 *>(P.conic_opacity)[r];
   t.u = m.x; t.v = m.y; t.A = co.x; t.beta = co.y; t.gamma = co.z;
   t.qb = __fmul_rn(reinterpret_cast<const float4 *>(P.rgb)[r].w, kBinMargin);
+  tile_hit_consts(t.A, t.beta, t.gamma, t.ab, t.inv_den);
   const int view = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
   t.W = cams[view].width; t.H = cams[view].height; t.toff = cams[view].tile_offset; t.gx = cams[view].grid_x;
   return t;
@@ -264,56 +245,96 @@ __device__ __forceinline__ bool candidate(const RecordTiles &t, uint32_t c, int 
   tile = (uint32_t)t.toff + ty * (uint32_t)t.gx + tx;
   const float X0 = (float)(tx * tw) + 0.5f, X1 = (float)min((int)(tx + 1) * tw, t.W) - 0.5f;
   const float Y0 = (float)(ty * th) + 0.5f, Y1 = (float)min((int)(ty + 1) * th, t.H) - 0.5f;
-  return tile_hit(t.u, t.v, t.A, t.beta, t.gamma, t.qb, X0, X1, Y0, Y1);
+  return tile_hit(t.u, t.v, t.A, t.beta, t.gamma, t.ab, t.inv_den, t.qb, X0, X1, Y0, Y1);
 }
 
-// One warp per depth-ordered record: count the candidate tiles that pass.
-__global__ void tile_count_kernel(gs_proj_t P, const uint32_t *__restrict__ order, const uint32_t *n_vis,
-                                  const gs_camera_t *__restrict__ cams, int n_views, int64_t n_per_view, int tw,
-                                  int th, uint32_t *__restrict__ counts) {
+// Warp-cooperative pass over the candidate tiles of 32 depth-ordered records at a
+// time: lane l loads record k0 + l (one round of independent loads), the 32
+// candidate lists are concatenated by a warp scan, and each lane then takes one
+// candidate per step, finding its record by a binary search over the scan and
+// reading that record's fields with shuffles. COUNT writes the hits per record;
+// EMIT writes (tile id, record) for every hit at the record's offset, in candidate
+// order.
+template <bool EMIT>
+__global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint32_t *__restrict__ order,
+                                                         const uint32_t *n_vis, const uint32_t *overflow,
+                                                         const gs_camera_t *__restrict__ cams, int n_views,
+                                                         int64_t n_per_view, int tw, int th,
+                                                         uint32_t *__restrict__ counts,
+                                                         const uint32_t *__restrict__ offsets,
+                                                         uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
+  __shared__ uint32_t s_run[8][32];   // hits so far per record of the warp's batch
+  if (EMIT && *overflow) return;
   const uint32_t nv = *n_vis;
-  const int lane = threadIdx.x & 31;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nv; k += nw) {
-    const RecordTiles t = record_tiles(P, cams, n_views, n_per_view, order[k]);
-    uint32_t cnt = 0;
-    for (uint32_t base = 0; base < t.n; base += 32) {
-      const uint32_t c = base + lane;
-      uint32_t tile;
-      const bool hit = c < t.n && candidate(t, c, tw, th, tile);
-      cnt += __popc(__ballot_sync(0xffffffffu, hit));
-    }
-    if (lane == 0) counts[k] = cnt;
-  }
-}
-
-// One warp per depth-ordered record: write (tile id, record) for every passing tile,
-// in candidate order, at the record's offset.
-__global__ void emit_kernel(gs_proj_t P, const uint32_t *__restrict__ order, const uint32_t *__restrict__ offsets,
-                            const uint32_t *n_vis, const uint32_t *overflow, const gs_camera_t *__restrict__ cams,
-                            int n_views, int64_t n_per_view, int tw, int th, uint32_t *__restrict__ dkeys,
-                            uint32_t *__restrict__ dvals) {
-  if (*overflow) return;
-  const uint32_t nv = *n_vis;
-  const int lane = threadIdx.x & 31;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
-  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nv; k += nw) {
-    const uint32_t r = order[k];
-    const RecordTiles t = record_tiles(P, cams, n_views, n_per_view, r);
-    uint32_t o = offsets[k];
-    for (uint32_t base = 0; base < t.n; base += 32) {
-      const uint32_t c = base + lane;
-      uint32_t tile = 0;
-      const bool hit = c < t.n && candidate(t, c, tw, th, tile);
-      const uint32_t b = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const uint32_t pos = o + __popc(b & lt);
-        dkeys[pos] = tile;
-        dvals[pos] = r;
-      }
-      o += __popc(b);
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < nv; k0 += nw * 32) {
+    const uint32_t k = k0 + lane;
+    RecordTiles t{};
+    uint32_t r = 0, out0 = 0;
+    if (k < nv) {
+      r = order[k];
+      t = record_tiles(P, cams, n_views, n_per_view, r);
+      if (EMIT) out0 = offsets[k];
     }
+    uint32_t incl = t.n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - t.n;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    s_run[wib][lane] = 0;
+    __syncwarp();
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      const uint32_t g = c0 + lane;
+      // owner: the last record j whose candidates start at or before g
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t e = __shfl_sync(0xffffffffu, excl, j + step);
+        if (j + step < 32 && e <= g) j += step;
+      }
+      RecordTiles o;
+      o.x0 = __shfl_sync(0xffffffffu, t.x0, j);
+      o.y0 = __shfl_sync(0xffffffffu, t.y0, j);
+      o.w = __shfl_sync(0xffffffffu, t.w, j);
+      o.n = __shfl_sync(0xffffffffu, t.n, j);
+      o.u = __shfl_sync(0xffffffffu, t.u, j);
+      o.v = __shfl_sync(0xffffffffu, t.v, j);
+      o.A = __shfl_sync(0xffffffffu, t.A, j);
+      o.beta = __shfl_sync(0xffffffffu, t.beta, j);
+      o.gamma = __shfl_sync(0xffffffffu, t.gamma, j);
+      o.qb = __shfl_sync(0xffffffffu, t.qb, j);
+      o.ab = __shfl_sync(0xffffffffu, t.ab, j);
+      o.inv_den = __shfl_sync(0xffffffffu, t.inv_den, j);
+      o.W = __shfl_sync(0xffffffffu, t.W, j);
+      o.H = __shfl_sync(0xffffffffu, t.H, j);
+      o.toff = __shfl_sync(0xffffffffu, t.toff, j);
+      o.gx = __shfl_sync(0xffffffffu, t.gx, j);
+      const uint32_t c = g - __shfl_sync(0xffffffffu, excl, j);
+      uint32_t tile = 0;
+      const bool hit = g < total && candidate(o, c, tw, th, tile);
+      const uint32_t same = __match_any_sync(0xffffffffu, (uint32_t)j);
+      const uint32_t hits = __ballot_sync(0xffffffffu, hit) & same;
+      if (EMIT) {
+        const uint32_t base_j = __shfl_sync(0xffffffffu, out0, j);
+        const uint32_t r_j = __shfl_sync(0xffffffffu, r, j);
+        if (hit) {
+          const uint32_t pos = base_j + s_run[wib][j] + __popc(hits & lt);
+          dkeys[pos] = tile;
+          dvals[pos] = r_j;
+        }
+      }
+      __syncwarp();
+      // the lowest lane of each owner group advances that record's running count
+      if ((same & lt) == 0) s_run[wib][j] += __popc(hits);
+      __syncwarp();
+    }
+    if (!EMIT && k < nv) counts[k] = s_run[wib][lane];
+    __syncwarp();
   }
 }
 
@@ -377,7 +398,7 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
   w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dv1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.block_sums = (uint64_t *)take(8 * kMaxBlocks);
-  w.hist = (uint32_t *)take(4 * (size_t)kRsBins * kMaxBlocks);
+  w.hist = (uint32_t *)take(4 * (size_t)kRsBins * (kMaxBlocks + 1));   // + digit totals
   w.counters = (uint32_t *)take(64);
   w.bytes = off;
   return w;
@@ -399,11 +420,11 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     uint32_t *ki = cur0 ? k0 : k1, *vi = cur0 ? v0 : v1, *ko = cur0 ? k1 : k0, *vo = cur0 ? v1 : v0;
     rs_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, d_n, d_skip, shift, mask, hist);
     GS_LAUNCH_CHECK();
-    rs_scan_kernel<<<1, 1024, 0, s>>>(hist, G, d_n, d_skip);
+    rs_scan_kernel<<<kRsBins, 32, 0, s>>>(hist, G, hist + (size_t)kRsBins * kMaxBlocks, d_skip);
     GS_LAUNCH_CHECK();
     const bool last = p == passes - 1;
     rs_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, (last && !keep_keys) ? nullptr : ko, vo, d_n, d_skip,
-                                                 shift, mask, hist);
+                                                 shift, mask, hist, hist + (size_t)kRsBins * kMaxBlocks);
     GS_LAUNCH_CHECK();
     cur0 = !cur0;
   }
@@ -453,8 +474,9 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   // 3. tiles hit per record, duplicate offsets in depth order, M and the capacity check
   const int64_t n_per_view = R / frame->n_views;
   const int eg = num_sms() * 8;
-  tile_count_kernel<<<eg, 256, 0, s>>>(*proj, order, n_vis, frame->cams_dev, frame->n_views, n_per_view,
-                                       frame->tile_w, frame->tile_h, w.counts);
+  candidates_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
+                                              n_per_view, frame->tile_w, frame->tile_h, w.counts, nullptr,
+                                              nullptr, nullptr);
   GS_LAUNCH_CHECK();
   TouchedOffsets to{w.counts, n_vis, w.offsets, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
   if (gs_status_t st = run_scan(to, w.block_sums, G, s)) return st;
@@ -463,9 +485,9 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int passes = (tile_bits + 7) / 8;
   uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
   const bool emit_to_A = (passes % 2) == 0;
-  emit_kernel<<<eg, 256, 0, s>>>(*proj, order, w.offsets, n_vis, overflow, frame->cams_dev, frame->n_views,
-                                 n_per_view, frame->tile_w, frame->tile_h, emit_to_A ? A_k : B_k,
-                                 emit_to_A ? A_v : B_v);
+  candidates_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
+                                             n_per_view, frame->tile_w, frame->tile_h, nullptr, w.offsets,
+                                             emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
   GS_LAUNCH_CHECK();
   // 5. stable sort by tile id
   bool res0 = true;

@@ -63,8 +63,12 @@ constexpr float kBinMargin = 1.002f;    // tile test keeps q_min <= q_max * 1.00
 // rounding is explicit so that the forward and backward kernels take identical
 // skip / stop decisions.
 struct Falloff {
-  float dx, dy, t, power, G, raw, alpha;
+  float dx, dy, t, G, raw, alpha;
 };
+
+// The quadratic form is non-negative by construction (A, gamma > 0), so no entry
+// needs the "exponent > 0" rejection; G = 2^(q * (-1/2 log2 e)).
+constexpr float kNegHalfLog2e = -0.72134752044448170f;
 
 __device__ __forceinline__ Falloff falloff(float u, float v, float A, float beta, float gamma, float o,
                                            float px, float py) {
@@ -73,8 +77,7 @@ __device__ __forceinline__ Falloff falloff(float u, float v, float A, float beta
   f.dy = __fsub_rn(v, py);
   f.t = __fmaf_rn(beta, f.dy, f.dx);
   const float q = __fmaf_rn(__fmul_rn(A, f.t), f.t, __fmul_rn(gamma, __fmul_rn(f.dy, f.dy)));
-  f.power = __fmul_rn(-0.5f, q);
-  f.G = ex2_approx(__fmul_rn(f.power, kLog2e));
+  f.G = ex2_approx(__fmul_rn(q, kNegHalfLog2e));
   f.raw = __fmul_rn(o, f.G);
   f.alpha = fminf(kAlphaMax, f.raw);
   return f;
@@ -90,13 +93,18 @@ __device__ __forceinline__ float qform_rn(float dx, float dy, float A, float bet
   return __fadd_rn(__fmul_rn(A, __fmul_rn(t, t)), __fmul_rn(gamma, __fmul_rn(dy, dy)));
 }
 
-__device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, float gamma, float qb, float X0,
-                                         float X1, float Y0, float Y1) {
+// ab = A beta and inv_den = 1 / (A beta^2 + gamma) are per-record constants
+// (tile_hit_consts); the fixed-dx edge minimiser is dy* = -(A beta dx) / (A beta^2 + gamma).
+__device__ __forceinline__ void tile_hit_consts(float A, float beta, float gamma, float &ab, float &inv_den) {
+  ab = __fmul_rn(A, beta);
+  inv_den = __fdiv_rn(1.f, __fadd_rn(__fmul_rn(ab, beta), gamma));
+}
+
+__device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, float gamma, float ab, float inv_den,
+                                         float qb, float X0, float X1, float Y0, float Y1) {
   const float dxl = __fsub_rn(u, X1), dxh = __fsub_rn(u, X0);
   const float dyl = __fsub_rn(v, Y1), dyh = __fsub_rn(v, Y0);
   if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return true;
-  const float ab = __fmul_rn(A, beta);
-  const float den = __fadd_rn(__fmul_rn(ab, beta), gamma);
   float m;
   {
     const float dx = fminf(fmaxf(-__fmul_rn(beta, dyl), dxl), dxh);
@@ -107,11 +115,11 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, 
     m = fminf(m, qform_rn(dx, dyh, A, beta, gamma));
   }
   {
-    const float dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(ab, dxl), den), dyl), dyh);
+    const float dy = fminf(fmaxf(-__fmul_rn(__fmul_rn(ab, dxl), inv_den), dyl), dyh);
     m = fminf(m, qform_rn(dxl, dy, A, beta, gamma));
   }
   {
-    const float dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(ab, dxh), den), dyl), dyh);
+    const float dy = fminf(fmaxf(-__fmul_rn(__fmul_rn(ab, dxh), inv_den), dyl), dyh);
     m = fminf(m, qform_rn(dxh, dy, A, beta, gamma));
   }
   return m <= qb;

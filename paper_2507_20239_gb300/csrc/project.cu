@@ -256,13 +256,29 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
   }
 }
 
-template <int DEG>
+// STAGED (sh_stride == (DEG+1)^2): each warp moves the SH rows of its 32 Gaussians
+// (and later their gradients) between global and shared memory with coalesced
+// accesses; rows are padded by one float so per-thread row access is conflict-free.
+template <int DEG, bool STAGED>
 __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
                                                           int n_views, gs_proj_t proj, gs_rec_grads_t rg,
                                                           gs_param_grads_t out, float *accum, int32_t *count) {
   constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int RW = 3 * K, RP = RW + 1;
+  __shared__ float s_sh[STAGED ? 4 * 32 * RP : 1];
   const int64_t n = P.n;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float *wsh = s_sh + (STAGED ? wib * 32 * RP : 0);
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = base + threadIdx.x;
+    const int64_t g0 = base + wib * 32;
+    const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
+    if (STAGED) {
+      const float *src = P.sh + g0 * RW;
+      for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
+      __syncwarp();
+    }
+    if (g < n) {
     const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
     float d_mean[3] = {0.f, 0.f, 0.f};
     float dM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // dL/dM, M = R S
@@ -277,7 +293,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     float qinv = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, M[9];
     Rot Rq;
-    const float *sh = P.sh + (int64_t)g * P.sh_stride * 3;
+    const float *sh = STAGED ? wsh + lane * RP : P.sh + (int64_t)g * P.sh_stride * 3;
     for (int v = 0; v < n_views; ++v) {
       const int64_t r = (int64_t)v * n + g;
       if (proj.radius[r] <= 0) continue;
@@ -421,17 +437,34 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
     out.d_log_scales[3 * g + 2] = d_ls[2];
     reinterpret_cast<float4 *>(out.d_quats)[g] = make_float4(d_q[0], d_q[1], d_q[2], d_q[3]);
     out.d_opacity_logits[g] = d_logit;
-    float *dsh = out.d_sh + (int64_t)g * P.sh_stride * 3;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      dsh[3 * k + 0] = d_sh[k][0];
-      dsh[3 * k + 1] = d_sh[k][1];
-      dsh[3 * k + 2] = d_sh[k][2];
-    }
-    for (int k = K; k < P.sh_stride; ++k) dsh[3 * k + 0] = dsh[3 * k + 1] = dsh[3 * k + 2] = 0.f;
     if (accum) {
       accum[g] = acc;
       count[g] = cnt;
+    }
+    if (STAGED) {
+      // this lane's row of wsh is only read by this lane: overwrite it in place
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        wsh[lane * RP + 3 * k + 0] = d_sh[k][0];
+        wsh[lane * RP + 3 * k + 1] = d_sh[k][1];
+        wsh[lane * RP + 3 * k + 2] = d_sh[k][2];
+      }
+    } else {
+      float *dsh = out.d_sh + (int64_t)g * P.sh_stride * 3;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        dsh[3 * k + 0] = d_sh[k][0];
+        dsh[3 * k + 1] = d_sh[k][1];
+        dsh[3 * k + 2] = d_sh[k][2];
+      }
+      for (int k = K; k < P.sh_stride; ++k) dsh[3 * k + 0] = dsh[3 * k + 1] = dsh[3 * k + 2] = 0.f;
+    }
+    }  // g < n
+    if (STAGED) {
+      __syncwarp();
+      float *dst = out.d_sh + g0 * RW;
+      for (int f = lane; f < rows * RW; f += 32) dst[f] = wsh[(f / RW) * RP + (f % RW)];
+      __syncwarp();
     }
   }
 }
@@ -454,6 +487,12 @@ __global__ void densify_accum_kernel(const float *__restrict__ d_mean2d, const i
     accum[g] = acc;
     count[g] = cnt;
   }
+}
+
+template <int DEG, bool STAGED>
+static void launch_bwd_k(int grid, cudaStream_t s, const gs_params_t &P, const gs_frame_t *frame, const gs_proj_t &proj,
+                         const gs_rec_grads_t &rg, const gs_param_grads_t &out, float *acc, int32_t *cnt) {
+  project_bwd_kernel<DEG, STAGED><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -508,11 +547,17 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_frame_
   if (params->n == 0) return GS_OK;
   const int grid = grid_for(params->n, 128);
   cudaStream_t s = as_stream(stream);
+  const int K = (params->sh_degree + 1) * (params->sh_degree + 1);
+  const bool staged = params->sh_stride == K;
   switch (params->sh_degree) {
-    case 0: project_bwd_kernel<0><<<grid, 128, 0, s>>>(*params, frame->cams_dev, frame->n_views, *proj, *rg, *out, densify_accum, densify_count); break;
-    case 1: project_bwd_kernel<1><<<grid, 128, 0, s>>>(*params, frame->cams_dev, frame->n_views, *proj, *rg, *out, densify_accum, densify_count); break;
-    case 2: project_bwd_kernel<2><<<grid, 128, 0, s>>>(*params, frame->cams_dev, frame->n_views, *proj, *rg, *out, densify_accum, densify_count); break;
-    default: project_bwd_kernel<3><<<grid, 128, 0, s>>>(*params, frame->cams_dev, frame->n_views, *proj, *rg, *out, densify_accum, densify_count); break;
+    case 0: staged ? launch_bwd_k<0, true>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count)
+                  : launch_bwd_k<0, false>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count); break;
+    case 1: staged ? launch_bwd_k<1, true>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count)
+                  : launch_bwd_k<1, false>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count); break;
+    case 2: staged ? launch_bwd_k<2, true>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count)
+                  : launch_bwd_k<2, false>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count); break;
+    default: staged ? launch_bwd_k<3, true>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count)
+                  : launch_bwd_k<3, false>(grid, s, *params, frame, *proj, *rg, *out, densify_accum, densify_count); break;
   }
   GS_LAUNCH_CHECK();
   return GS_OK;

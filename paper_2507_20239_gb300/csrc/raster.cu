@@ -1,9 +1,12 @@
 // Front-to-back alpha compositing (the paper's Eq. 2) and its gradient.
 //
-// One CTA per tile, two horizontally adjacent pixels per thread. The tile's
-// depth-ordered list is consumed in batches of one record per thread, staged in
-// shared memory; a pixel stops before the entry that would drive its
-// transmittance below 1e-4 and the CTA leaves once every pixel has stopped.
+// One CTA per tile, two horizontally adjacent pixels per thread; each warp owns an
+// 8x8 block of the tile. The tile's depth-ordered list is consumed in batches of one
+// record per thread, staged in shared memory together with a mask of the 8x8
+// blocks the record's footprint reaches (the binning's exact ellipse-box test), so a
+// warp skips the records that cannot touch its pixels. A pixel stops before the
+// entry that would drive its transmittance below 1e-4 and the CTA leaves once every
+// pixel has stopped.
 //
 // The backward pass re-walks the list front to back with exactly the forward's
 // FP32 decisions (no stored stop index) and needs, per pixel, only <dL/dout, out>:
@@ -34,6 +37,43 @@ __device__ __forceinline__ TileCoord tile_coord(const gs_camera_t *cams, int n_v
   return c;
 }
 
+// Pixel mapping: warp w owns the 8x8 block (w % (TW/8), w / (TW/8)) of the tile;
+// lane l owns pixels (2 (l % 4), l / 4) and (2 (l % 4) + 1, l / 4) of that block.
+template <int TW>
+__device__ __forceinline__ void pixel_of(int t, int &lx, int &ly) {
+  const int w = t >> 5, l = t & 31;
+  lx = (w % (TW / 8)) * 8 + 2 * (l & 3);
+  ly = (w / (TW / 8)) * 8 + (l >> 2);
+}
+
+// Stage list entry r: position, factored conic + opacity, colour; colour.w holds the
+// mask of the tile's 8x8 blocks whose pixel centres the footprint ellipse meets (the
+// binning's conservative test), so a warp can skip records that miss its block.
+template <int TW, int TH>
+__device__ __forceinline__ void stage(const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
+                                      const float4 *__restrict__ rgb, uint32_t r, int x0, int y0, int W, int H,
+                                      float2 &xy, float4 &co, float4 &c) {
+  xy = mean2d[r];
+  co = conic_o[r];
+  c = rgb[r];
+  uint32_t m = 1u;
+  if (TW * TH > 64) {
+    float ab, inv_den;
+    tile_hit_consts(co.x, co.y, co.z, ab, inv_den);
+    const float qb = __fmul_rn(c.w, kBinMargin);
+    m = 0u;
+#pragma unroll
+    for (int b = 0; b < TW * TH / 64; ++b) {
+      const int bx = x0 + (b % (TW / 8)) * 8, by = y0 + (b / (TW / 8)) * 8;
+      if (bx >= W || by >= H) continue;
+      const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + 8, W) - 0.5f;
+      const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + 8, H) - 0.5f;
+      if (tile_hit(xy.x, xy.y, co.x, co.y, co.z, ab, inv_den, qb, X0, X1, Y0, Y1)) m |= 1u << b;
+    }
+  }
+  c.w = __uint_as_float(m);
+}
+
 // COUNT: instead of the image, write per pixel (entries examined up to and including
 // the one that triggers the cut-off, entries composited) to counts[2 * pixel].
 template <int TW, int TH, bool COUNT>
@@ -42,14 +82,16 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
     uint32_t *__restrict__ stop_out, uint32_t *__restrict__ counts) {
-  constexpr int NT = TW * TH / 2, HW = TW / 2;
+  constexpr int NT = TW * TH / 2;
   __shared__ float2 s_xy[NT];
   __shared__ float4 s_co[NT];
   __shared__ float4 s_rgb[NT];
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
-  const int t = threadIdx.x;
-  const int py = tc.ty * TH + t / HW;
-  const int px = tc.tx * TW + 2 * (t % HW);
+  const int t = threadIdx.x, warp = t >> 5;
+  int lx, ly;
+  pixel_of<TW>(t, lx, ly);
+  const int py = tc.ty * TH + ly;
+  const int px = tc.tx * TW + lx;
   const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
   const float fy = (float)py + 0.5f, fx0 = (float)px + 0.5f, fx1 = (float)px + 1.5f;
   float T0 = 1.f, T1 = 1.f;
@@ -61,22 +103,20 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
   const int n = (int)(rg.y - rg.x);
   for (int base = 0; base < n; base += NT) {
     if (__syncthreads_count(!(done0 && done1)) == 0) break;
-    if (base + t < n) {
-      const uint32_t r = vals[rg.x + base + t];
-      s_xy[t] = mean2d[r];
-      s_co[t] = conic_o[r];
-      s_rgb[t] = rgb[r];
-    }
+    if (base + t < n)
+      stage<TW, TH>(mean2d, conic_o, rgb, vals[rg.x + base + t], tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t],
+                    s_rgb[t]);
     __syncthreads();
     if (__all_sync(0xffffffffu, done0 && done1)) continue;
     const int cnt = min(NT, n - base);
     for (int j = 0; j < cnt; ++j) {
+      if (!COUNT && !((__float_as_uint(s_rgb[j].w) >> warp) & 1u)) continue;   // warp-uniform skip
       const float2 xy = s_xy[j];
       const float4 co = s_co[j];
       if (!done0) {
         if (COUNT) ++ex0;
         const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx0, fy);
-        if (f.power <= 0.f && f.alpha >= kAlphaMin) {
+        if (f.alpha >= kAlphaMin) {
           const float Tn = __fmul_rn(T0, __fsub_rn(1.f, f.alpha));
           if (Tn < kTMin) {
             done0 = true;
@@ -93,7 +133,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
       if (!done1) {
         if (COUNT) ++ex1;
         const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx1, fy);
-        if (f.power <= 0.f && f.alpha >= kAlphaMin) {
+        if (f.alpha >= kAlphaMin) {
           const float Tn = __fmul_rn(T1, __fsub_rn(1.f, f.alpha));
           if (Tn < kTMin) {
             done1 = true;
@@ -177,7 +217,7 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, co
                                         const float4 c, float *v) {
   if (p.done) return false;
   const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, p.fx, fy);
-  if (!(f.power <= 0.f && f.alpha >= kAlphaMin)) return false;
+  if (!(f.alpha >= kAlphaMin)) return false;
   const float one_m = __fsub_rn(1.f, f.alpha);
   const float Tn = __fmul_rn(p.T, one_m);
   if (Tn < kTMin) {
@@ -196,12 +236,13 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, co
     v[5] = fmaf(f.G, dLda, v[5]);
     // P = -1/2 (A t^2 + gamma dy^2), t = dx + beta dy, dx = u - p_x, dy = v - p_y
     const float dP = dLda * f.raw;
-    const float At = co.x * f.t;
-    v[0] -= dP * At;
-    v[1] -= dP * fmaf(At, co.y, co.z * f.dy);
-    v[2] -= 0.5f * dP * f.t * f.t;
-    v[3] -= dP * At * f.dy;
-    v[4] -= 0.5f * dP * f.dy * f.dy;
+    const float At = co.x * f.t, gdy = co.z * f.dy;
+    const float hP = -0.5f * dP;
+    v[0] = fmaf(-dP, At, v[0]);
+    v[1] = fmaf(-dP, fmaf(At, co.y, gdy), v[1]);
+    v[2] = fmaf(hP * f.t, f.t, v[2]);
+    v[3] = fmaf(-dP * At, f.dy, v[3]);
+    v[4] = fmaf(hP * f.dy, f.dy, v[4]);
   }
   return true;
 }
@@ -212,16 +253,18 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image, float *__restrict__ g_mean2d,
     float *__restrict__ g_co, float *__restrict__ g_rgb) {
-  constexpr int NT = TW * TH / 2, HW = TW / 2;
+  constexpr int NT = TW * TH / 2;
   __shared__ float2 s_xy[NT];
   __shared__ float4 s_co[NT];
   __shared__ float4 s_rgb[NT];
   __shared__ uint32_t s_rec[NT];
   __shared__ float s_acc[NT * 9];
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
-  const int t = threadIdx.x, lane = t & 31;
-  const int py = tc.ty * TH + t / HW;
-  const int px = tc.tx * TW + 2 * (t % HW);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int lx, ly;
+  pixel_of<TW>(t, lx, ly);
+  const int py = tc.ty * TH + ly;
+  const int px = tc.tx * TW + lx;
   const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
   const float fy = (float)py + 0.5f;
   const int64_t plane = (int64_t)tc.W * tc.H;
@@ -246,22 +289,25 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
     if (t < cnt) {
       const uint32_t r = vals[rg.x + base + t];
       s_rec[t] = r;
-      s_xy[t] = mean2d[r];
-      s_co[t] = conic_o[r];
-      s_rgb[t] = rgb[r];
+      stage<TW, TH>(mean2d, conic_o, rgb, r, tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t], s_rgb[t]);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) s_acc[k * NT + t] = 0.f;
     __syncthreads();
     if (!__all_sync(0xffffffffu, q0.done && q1.done)) {
+      float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int j = 0; j < cnt; ++j) {
+        const float4 c = s_rgb[j];
+        if (!((__float_as_uint(c.w) >> warp) & 1u)) continue;   // warp-uniform skip
         const float2 xy = s_xy[j];
         const float4 co = s_co[j];
-        const float4 c = s_rgb[j];
-        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         bool any = pix_bwd(q0, fy, xy, co, c, v);
         any |= pix_bwd(q1, fy, xy, co, c, v);
-        if (__any_sync(0xffffffffu, any)) warp_reduce9_add(v, s_acc + j * 9, lane);
+        if (__any_sync(0xffffffffu, any)) {
+          warp_reduce9_add(v, s_acc + j * 9, lane);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) v[k] = 0.f;   // lanes without a contribution kept zeros
+        }
       }
     }
     __syncthreads();

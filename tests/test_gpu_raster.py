@@ -47,10 +47,13 @@ def _tile_mask(cam, tile, tiles):
     return m
 
 
-def _compare_fwd(o, img, T, stop, mask=None, counts=None):
+def _compare_fwd(o, img, T, stop, mask=None, counts=None, max_flag_frac=1e-2):
     """Image and T within 1e-4, stop index and per-pixel work counts exact, on every
     pixel the oracle does not flag; flagged pixels (a cut-off decision within the
-    FP32 error bound of its threshold) must be rare and within 1/255 + 1e-4."""
+    FP32 error bound of its threshold) must be rare and within 1/255 + 1e-4.
+    The expected flagged fraction grows with the entries a pixel examines (each has
+    a ~1e-6 chance of lying inside the alpha-floor window), hence the larger cap for
+    the dense full-size tiles."""
     flag = o["flag"]
     sel = ~flag if mask is None else (~flag & mask)
     err = np.abs(img - o["image"]).max(0)
@@ -61,7 +64,7 @@ def _compare_fwd(o, img, T, stop, mask=None, counts=None):
         assert np.array_equal(counts[..., 0][sel], o["n_examined"][sel])
         assert np.array_equal(counts[..., 1][sel], o["n_contrib"][sel])
     fl = flag if mask is None else (flag & mask)
-    assert fl.sum() <= max(2, 1e-2 * (sel.sum() + fl.sum())), fl.sum()
+    assert fl.sum() <= max(2, max_flag_frac * (sel.sum() + fl.sum())), fl.sum()
     if fl.sum():
         assert err[fl].max() < 1 / 255 + IMG_TOL
     return int(fl.sum())
@@ -137,7 +140,7 @@ def test_raster_full_size_sampled_tiles():
     o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
     counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
-                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts)
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts, max_flag_frac=5e-2)
     rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda())
     torch.cuda.synchronize()
     got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
