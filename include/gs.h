@@ -272,6 +272,29 @@ gs_status_t gs_densify_select(const gs_densify_cfg_t *cfg, const float *log_scal
                               float *d_tau_logit, int64_t *d_new_n, void *ws, size_t ws_bytes,
                               gs_stream_t stream);
 
+/* Allocation-free variant of gs_densify_select (the paper has no counterpart; this is
+ * a library-integration entry point). For callers that cannot allocate device memory
+ * for a workspace -- custom operators and plugins running inside another runtime's
+ * execution callbacks, where allocating is forbidden or would bypass that runtime's
+ * memory accounting, and fixed-budget deployments that must not grow their device
+ * footprint at run time. Same arguments, results and stream semantics as
+ * gs_densify_select, without ws / ws_bytes: the scratch (1,056 bytes: the selection
+ * counters and a 256-bin histogram) lives in a file-scope device array of the
+ * library that every GPU loading the library holds until the process exits.
+ *  - n must not exceed GS_DENSIFY_SELECT_STATIC_MAX_N (the scratch's 32-bit
+ *    histogram counts); larger n returns GS_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address on the current
+ *    device (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture on the device.
+ *  - Every call shares the one array and clears it on its stream before use; calls
+ *    that overlap on the GPU (different streams, or concurrent threads) race on it.
+ *  - Calls no cudaMalloc, cudaFree or allocating routine. */
+#define GS_DENSIFY_SELECT_STATIC_MAX_N (1ll << 30)
+gs_status_t gs_densify_select_static(const gs_densify_cfg_t *cfg, const float *log_scales,
+                                     const float *opacity_logits, const float *accum,
+                                     const int32_t *count, int64_t n, uint8_t *split, uint8_t *clone,
+                                     float *d_tau_logit, int64_t *d_new_n, gs_stream_t stream);
+
 /* One extra per-Gaussian float array carried through compaction (e.g. an optimiser
  * moment): survivors keep their row, new rows are zero. */
 typedef struct {

@@ -12,6 +12,8 @@
 // Every predicate is evaluated in FP32 with one rounding per operation.
 #include <math.h>
 
+#include <mutex>
+
 #include "gs_common.cuh"
 #include "scan.cuh"
 
@@ -375,6 +377,75 @@ extern "C" gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_pa
   }
   scatter_kernel<<<dgrid(in->n), kSelThreads, 0, s>>>(*cfg, *in, split, clone, d_tau_logit, *out, el, w.pos_s,
                                                       w.pos_c, w.pos_p, w.totals, out_capacity, d_new_n, d_error);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+// Some callers cannot allocate device memory for a workspace: custom operators and
+// plugins that run inside another runtime's execution callbacks, where allocating
+// is forbidden or would bypass the host runtime's memory accounting, and
+// fixed-budget deployments that must not grow their device footprint at run time.
+// gs_densify_select_static serves them with its scratch (the selection state: two
+// counters, the radix-select prefix and a 256-bin histogram) in this file-scope
+// device array instead of a caller workspace. Every GPU that loads the library holds
+// it until the process exits.
+static __device__ __align__(256) SelectState g_select_scratch;
+
+namespace {
+constexpr int kMaxScratchDevices = 64;
+std::mutex g_scratch_mutex;
+SelectState *g_scratch_addr[kMaxScratchDevices] = {};
+}  // namespace
+
+// Device address of g_select_scratch on the current device. The array's name is
+// only a host-side stand-in for it, so the address is looked up once per device
+// (with that device current) and cached.
+static gs_status_t static_select_scratch(SelectState **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxScratchDevices) return GS_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_addr[dev] == nullptr) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+    if (e != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
+    g_scratch_addr[dev] = static_cast<SelectState *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return GS_OK;
+}
+
+extern "C" gs_status_t gs_densify_select_static(const gs_densify_cfg_t *cfg, const float *log_scales,
+                                                const float *opacity_logits, const float *accum,
+                                                const int32_t *count, int64_t n, uint8_t *split, uint8_t *clone,
+                                                float *d_tau_logit, int64_t *d_new_n, gs_stream_t stream) {
+  if (!cfg || !log_scales || !opacity_logits || !accum || !count || n <= 0 || !split || !clone || !d_tau_logit ||
+      !d_new_n)
+    return GS_ERR_INVALID_ARG;
+  if (n > GS_DENSIFY_SELECT_STATIC_MAX_N) return GS_ERR_INVALID_ARG;   // beyond the scratch's counters
+  if (cfg->mode < 0 || cfg->mode > 3) return GS_ERR_INVALID_ARG;
+  if (cfg->prune_adaptive && !(cfg->prune_ratio > 0.0 && cfg->prune_ratio < 1.0)) return GS_ERR_INVALID_ARG;
+  SelectState *st = nullptr;
+  if (gs_status_t e = static_select_scratch(&st)) return e;
+  cudaStream_t s = as_stream(stream);
+  // the previous call's contents are still there: clear the counters and histogram
+  GS_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(SelectState), s));
+  const int G = dgrid(n);
+  select_kernel<<<G, kSelThreads, 0, s>>>(*cfg, log_scales, accum, count, n, split, clone, st);
+  GS_LAUNCH_CHECK();
+  if (cfg->prune_adaptive) {
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      kth_hist_kernel<<<G, kSelThreads, 0, s>>>(opacity_logits, split, clone, n, shift, st);
+      GS_LAUNCH_CHECK();
+      kth_find_kernel<<<1, 32, 0, s>>>(shift, cfg->prune_ratio, st);
+      GS_LAUNCH_CHECK();
+    }
+  }
+  tau_kernel<<<1, 32, 0, s>>>(*cfg, st, d_tau_logit);
+  GS_LAUNCH_CHECK();
+  count_keep_kernel<<<G, kSelThreads, 0, s>>>(opacity_logits, split, clone, n, d_tau_logit, st, d_new_n);
+  GS_LAUNCH_CHECK();
+  publish_kernel<<<1, 32, 0, s>>>(st, d_new_n);
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
