@@ -441,14 +441,14 @@ def oracle_view_seconds(sc, n_tiles_sample, seed=0):
     t_proj = time.perf_counter() - t0
     gx, gy = pr["grid"]
     t0 = time.perf_counter()
-    lists = oras.tile_lists(pr["rect"], pr["depth"].astype(np.float32), gx, gy)
+    lists = oras.tile_lists(opipe.proj_record_arrays(pr), cam.width, cam.height)
     t_bin = time.perf_counter() - t0
     rng = np.random.default_rng(seed)
     busy = [t for t, l in lists.items() if len(l)]
     tiles = sorted(rng.choice(busy, min(n_tiles_sample, len(busy)), replace=False).tolist())
     d_image = rng.normal(0, 1, (3, cam.height, cam.width))
     t0 = time.perf_counter()
-    oras.raster_vjp(pr["mean2d"], pr["conic"], pr["opacity"], pr["rgb"], lists, cam.width, cam.height, d_image,
+    oras.raster_vjp(pr["mean2d"], pr["conic_f"], pr["opacity"], pr["rgb"], lists, cam.width, cam.height, d_image,
                     tiles=tiles)
     t_tiles = time.perf_counter() - t0
     n_s = min(sc.n, 100_000)
