@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--cpu-sample-tiles", type=int, default=48)
+    ap.add_argument("--cpu-sample-tiles", type=int, default=160)
     ap.add_argument("--n", type=int, default=1_500_000)
     ap.add_argument("--tile", default="16x16", help="tile shape WxH (16x16, 8x8, 16x32, 32x16)")
     ap.add_argument("--quick", action="store_true",
@@ -355,11 +355,17 @@ def tile_sync_stats(frame, counts):
 
 
 def load_traffic(kernel):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if present."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, used only
+    while the rasterizer sources are the ones the counters were taken on."""
+    import hashlib
     try:
-        with open(path) as f:
-            return json.load(f).get(kernel)
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        csrc = os.path.join(ROOT, "paper_2507_20239_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in ("raster.cu", "gs_common.cuh"))
+        if hashlib.sha256(src).hexdigest() != t.get("source_sha256"):
+            return None
+        return t.get(kernel)
     except Exception:
         return None
 
