@@ -28,8 +28,8 @@ namespace gs {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 4096 keys per tile
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 keys per tile
 constexpr int kRsBins = 256;
 
 // ------------------------------------------------------------------ LSD radix sort pass
@@ -88,10 +88,10 @@ __global__ void __launch_bounds__(32) rs_scan_kernel(uint32_t *hist, int G, uint
   if (lane == 0) totals[d] = carry;
 }
 
-// Stable scatter. Each warp ranks a contiguous 512-key slice of the tile, 32 keys per
+// Stable scatter. Each warp ranks a contiguous slice of the tile, 32 keys per
 // step in order, with __match_any_sync; slices are then offset by the warps before
 // them, staged in shared memory in digit order and written out coalesced.
-__global__ void __launch_bounds__(kRsThreads) rs_downsweep_kernel(
+__global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *d_n, const uint32_t *d_skip, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_kernel(
     uint32_t k[kRsItems], v[kRsItems], dig[kRsItems], rank[kRsItems];
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
-      const uint32_t li = warp * (32 * kRsItems) + j * 32 + lane;
+      const uint32_t li = warp * (32 * kRsItems) + j * 32 + lane;   // warp slice of 32 * kRsItems keys
       const bool valid = li < tile_n;
       k[j] = valid ? keys_in[tb + li] : 0u;
       v[j] = valid ? vals_in[tb + li] : 0u;
@@ -405,11 +405,18 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
 }
 
 
+// Blocks of the radix passes: four per SM (the downsweep holds 8 keys per thread).
+static int radix_blocks() {
+  const int g = 4 * num_sms();
+  return g > kMaxBlocks ? kMaxBlocks : g;
+}
+
 // Stable LSD radix sort of (key, val) pairs on bits [0, n_bits), ping-ponging between
 // buffer 0 and 1; returns in *in_b0 whether the result is in buffer 0.
 static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *d_n,
                               const uint32_t *d_skip, int n_bits, bool keep_keys, uint32_t *hist, int G,
                               cudaStream_t s, bool *in_b0) {
+  G = radix_blocks();
   const int passes = (n_bits + 7) / 8;
   const int bits = (n_bits + passes - 1) / passes;
   bool cur0 = true;

@@ -24,60 +24,32 @@ constexpr float kC3c = 0.4570457994644658f;   // sqrt(21/(2 pi))/4    y(5z^2-1),
 constexpr float kC3d = 0.3731763325901154f;   // sqrt(7/pi)/4         z(5z^2-3)
 constexpr float kC3e = 1.445305721320277f;    // sqrt(105/pi)/4       z(x^2-y^2)
 
-template <int DEG>
-__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
-  Y[0] = kC0;
+// Visit every basis function k < (DEG+1)^2 with its value and its gradient w.r.t.
+// the (unnormalised) direction components, without materialising arrays:
+// f(k, Y, dY/dx, dY/dy, dY/dz).
+template <int DEG, typename F>
+__device__ __forceinline__ void sh_visit(float x, float y, float z, F &&f) {
+  f(0, kC0, 0.f, 0.f, 0.f);
   if (DEG >= 1) {
-    Y[1] = -kC1 * y;
-    Y[2] = kC1 * z;
-    Y[3] = -kC1 * x;
+    f(1, -kC1 * y, 0.f, -kC1, 0.f);
+    f(2, kC1 * z, 0.f, 0.f, kC1);
+    f(3, -kC1 * x, -kC1, 0.f, 0.f);
   }
   if (DEG >= 2) {
     const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = kC2a * x * y;
-    Y[5] = -kC2a * y * z;
-    Y[6] = kC2b * (3.f * zz - 1.f);
-    Y[7] = -kC2a * x * z;
-    Y[8] = kC2c * (xx - yy);
+    f(4, kC2a * x * y, kC2a * y, kC2a * x, 0.f);
+    f(5, -kC2a * y * z, 0.f, -kC2a * z, -kC2a * y);
+    f(6, kC2b * (3.f * zz - 1.f), 0.f, 0.f, 6.f * kC2b * z);
+    f(7, -kC2a * x * z, -kC2a * z, 0.f, -kC2a * x);
+    f(8, kC2c * (xx - yy), 2.f * kC2c * x, -2.f * kC2c * y, 0.f);
     if (DEG >= 3) {
-      Y[9] = -kC3a * y * (3.f * xx - yy);
-      Y[10] = kC3b * x * y * z;
-      Y[11] = -kC3c * y * (5.f * zz - 1.f);
-      Y[12] = kC3d * z * (5.f * zz - 3.f);
-      Y[13] = -kC3c * x * (5.f * zz - 1.f);
-      Y[14] = kC3e * z * (xx - yy);
-      Y[15] = -kC3a * x * (xx - 3.f * yy);
-    }
-  }
-}
-
-// d/d(x, y, z) of each polynomial above, weighted by w[k], accumulated into g.
-template <int DEG>
-__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float *w, float &gx,
-                                             float &gy, float &gz) {
-  gx = 0.f; gy = 0.f; gz = 0.f;
-  if (DEG >= 1) {
-    gy += -kC1 * w[1];
-    gz += kC1 * w[2];
-    gx += -kC1 * w[3];
-  }
-  if (DEG >= 2) {
-    gx += kC2a * y * w[4];           gy += kC2a * x * w[4];
-    gy += -kC2a * z * w[5];          gz += -kC2a * y * w[5];
-    gz += 6.f * kC2b * z * w[6];
-    gx += -kC2a * z * w[7];          gz += -kC2a * x * w[7];
-    gx += 2.f * kC2c * x * w[8];     gy += -2.f * kC2c * y * w[8];
-    if (DEG >= 3) {
-      const float xx = x * x, yy = y * y, zz = z * z;
-      gx += -6.f * kC3a * x * y * w[9];            gy += -3.f * kC3a * (xx - yy) * w[9];
-      gx += kC3b * y * z * w[10];                  gy += kC3b * x * z * w[10];
-      gz += kC3b * x * y * w[10];
-      gy += -kC3c * (5.f * zz - 1.f) * w[11];      gz += -10.f * kC3c * y * z * w[11];
-      gz += kC3d * (15.f * zz - 3.f) * w[12];
-      gx += -kC3c * (5.f * zz - 1.f) * w[13];      gz += -10.f * kC3c * x * z * w[13];
-      gx += 2.f * kC3e * x * z * w[14];            gy += -2.f * kC3e * y * z * w[14];
-      gz += kC3e * (xx - yy) * w[14];
-      gx += -3.f * kC3a * (xx - yy) * w[15];       gy += 6.f * kC3a * x * y * w[15];
+      f(9, -kC3a * y * (3.f * xx - yy), -6.f * kC3a * x * y, -3.f * kC3a * (xx - yy), 0.f);
+      f(10, kC3b * x * y * z, kC3b * y * z, kC3b * x * z, kC3b * x * y);
+      f(11, -kC3c * y * (5.f * zz - 1.f), 0.f, -kC3c * (5.f * zz - 1.f), -10.f * kC3c * y * z);
+      f(12, kC3d * z * (5.f * zz - 3.f), 0.f, 0.f, kC3d * (15.f * zz - 3.f));
+      f(13, -kC3c * x * (5.f * zz - 1.f), -kC3c * (5.f * zz - 1.f), 0.f, -10.f * kC3c * x * z);
+      f(14, kC3e * z * (xx - yy), 2.f * kC3e * x * z, -2.f * kC3e * y * z, kC3e * (xx - yy));
+      f(15, -kC3a * x * (xx - 3.f * yy), -3.f * kC3a * (xx - yy), 6.f * kC3a * x * y, 0.f);
     }
   }
 }
@@ -169,7 +141,6 @@ __device__ __forceinline__ void camera_centre(const gs_camera_t &cam, float &cx,
 template <int DEG>
 __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
                                                           int n_views, int tile_w, int tile_h, gs_proj_t out) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const int64_t R = (int64_t)n_views * P.n;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -233,16 +204,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
     float dx = mx - ccx, dy = my - ccy, dz = mz - ccz;
     const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= il; dy *= il; dz *= il;
-    float Y[K];
-    sh_basis<DEG>(dx, dy, dz, Y);
     const float *sh = P.sh + (int64_t)g * P.sh_stride * 3;
     float cr = 0.5f, cg = 0.5f, cb = 0.5f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      cr = fmaf(Y[k], sh[3 * k + 0], cr);
-      cg = fmaf(Y[k], sh[3 * k + 1], cg);
-      cb = fmaf(Y[k], sh[3 * k + 2], cb);
-    }
+    sh_visit<DEG>(dx, dy, dz, [&](int k, float Y, float, float, float) {
+      cr = fmaf(Y, sh[3 * k + 0], cr);
+      cg = fmaf(Y, sh[3 * k + 1], cg);
+      cb = fmaf(Y, sh[3 * k + 2], cb);
+    });
     const uint8_t cl = (cr < 0.f ? 1 : 0) | (cg < 0.f ? 2 : 0) | (cb < 0.f ? 4 : 0);
     const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
     reinterpret_cast<float2 *>(out.mean2d)[r] = make_float2(u, vv);
@@ -256,36 +224,19 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
   }
 }
 
-// STAGED (sh_stride == (DEG+1)^2): each warp moves the SH rows of its 32 Gaussians
-// (and later their gradients) between global and shared memory with coalesced
-// accesses; rows are padded by one float so per-thread row access is conflict-free.
-template <int DEG, bool STAGED>
-__global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
-                                                          int n_views, gs_proj_t proj, gs_rec_grads_t rg,
-                                                          gs_param_grads_t out, float *accum, int32_t *count) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int RW = 3 * K, RP = RW + 1;
-  __shared__ float s_sh[STAGED ? 4 * 32 * RP : 1];
+// Projection VJP, geometric part: conic, pixel mean and opacity gradients of every
+// view -> means (through t = W mu + t_w and J), log-scales, quaternion, opacity
+// logit; the densification statistic is fused. The colour part is project_bwd_sh.
+__global__ void __launch_bounds__(128, 6) project_bwd_geom_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
+                                                               int n_views, gs_proj_t proj, gs_rec_grads_t rg,
+                                                               gs_param_grads_t out, float *accum, int32_t *count) {
   const int64_t n = P.n;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float *wsh = s_sh + (STAGED ? wib * 32 * RP : 0);
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = base + threadIdx.x;
-    const int64_t g0 = base + wib * 32;
-    const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
-    if (STAGED) {
-      const float *src = P.sh + g0 * RW;
-      for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
-      __syncwarp();
-    }
-    if (g < n) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    {
     const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
     float d_mean[3] = {0.f, 0.f, 0.f};
     float dM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // dL/dM, M = R S
     float d_logit = 0.f;
-    float d_sh[K][3];
-#pragma unroll
-    for (int k = 0; k < K; ++k) d_sh[k][0] = d_sh[k][1] = d_sh[k][2] = 0.f;
     float acc = accum ? accum[g] : 0.f;
     int cnt = count ? count[g] : 0;
     bool any = false;
@@ -293,7 +244,6 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     float qinv = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, M[9];
     Rot Rq;
-    const float *sh = STAGED ? wsh + lane * RP : P.sh + (int64_t)g * P.sh_stride * 3;
     for (int v = 0; v < n_views; ++v) {
       const int64_t r = (int64_t)v * n + g;
       if (proj.radius[r] <= 0) continue;
@@ -313,7 +263,6 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
       project_cov(cam, M, G);
       const float2 gm = reinterpret_cast<const float2 *>(rg.d_mean2d)[r];
       const float4 gco = reinterpret_cast<const float4 *>(rg.d_conic_opacity)[r];
-      const float4 grgb = reinterpret_cast<const float4 *>(rg.d_rgb)[r];
       if (accum) {
         const float gx = __fmul_rn(gm.x, 0.5f * (float)cam.width);
         const float gy = __fmul_rn(gm.y, 0.5f * (float)cam.height);
@@ -374,29 +323,6 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
       // opacity = sigmoid(logit)
       const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
       d_logit += gco.w * o * (1.f - o);
-      // SH colour (zero through a clamped channel) and its direction dependence
-      const uint8_t cl = proj.clamped[r];
-      const float g0 = (cl & 1) ? 0.f : grgb.x, g1 = (cl & 2) ? 0.f : grgb.y, g2 = (cl & 4) ? 0.f : grgb.z;
-      float ccx, ccy, ccz;
-      camera_centre(cam, ccx, ccy, ccz);
-      float ex = mx - ccx, ey = my - ccy, ez = mz - ccz;
-      const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
-      const float dxn = ex * il, dyn = ey * il, dzn = ez * il;
-      float Y[K], w[K];
-      sh_basis<DEG>(dxn, dyn, dzn, Y);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        d_sh[k][0] += g0 * Y[k];
-        d_sh[k][1] += g1 * Y[k];
-        d_sh[k][2] += g2 * Y[k];
-        w[k] = g0 * sh[3 * k + 0] + g1 * sh[3 * k + 1] + g2 * sh[3 * k + 2];
-      }
-      float gdx, gdy, gdz;
-      sh_basis_vjp<DEG>(dxn, dyn, dzn, w, gdx, gdy, gdz);
-      const float dd = gdx * dxn + gdy * dyn + gdz * dzn;
-      d_mean[0] += (gdx - dd * dxn) * il;
-      d_mean[1] += (gdy - dd * dyn) * il;
-      d_mean[2] += (gdz - dd * dzn) * il;
     }
     float d_ls[3] = {0.f, 0.f, 0.f};
     float d_q[4] = {0.f, 0.f, 0.f, 0.f};
@@ -441,29 +367,104 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(gs_params_t P, const g
       accum[g] = acc;
       count[g] = cnt;
     }
-    if (STAGED) {
-      // this lane's row of wsh is only read by this lane: overwrite it in place
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        wsh[lane * RP + 3 * k + 0] = d_sh[k][0];
-        wsh[lane * RP + 3 * k + 1] = d_sh[k][1];
-        wsh[lane * RP + 3 * k + 2] = d_sh[k][2];
-      }
-    } else {
-      float *dsh = out.d_sh + (int64_t)g * P.sh_stride * 3;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        dsh[3 * k + 0] = d_sh[k][0];
-        dsh[3 * k + 1] = d_sh[k][1];
-        dsh[3 * k + 2] = d_sh[k][2];
-      }
-      for (int k = K; k < P.sh_stride; ++k) dsh[3 * k + 0] = dsh[3 * k + 1] = dsh[3 * k + 2] = 0.f;
     }
-    }  // g < n
+  }
+}
+
+// Projection VJP, colour part: SH coefficient gradients (zero through a clamped
+// channel) and the colour's dependence on the viewing direction, added to the
+// mean gradients that project_bwd_geom_kernel wrote. STAGED (sh_stride ==
+// (DEG+1)^2): each warp moves the SH rows of its 32 Gaussians and their gradients
+// between global and shared memory with coalesced accesses (rows padded by one float).
+// ONE_VIEW: with a single view each coefficient's gradient is written once, right
+// after the coefficient has been read, so it overwrites the staged row in place and
+// one shared buffer suffices (twice the resident blocks).
+template <int DEG, bool STAGED, bool ONE_VIEW>
+__global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
+    gs_params_t P, const gs_camera_t *__restrict__ cams, int n_views, gs_proj_t proj, gs_rec_grads_t rg,
+    gs_param_grads_t out) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int RW = 3 * K, RP = RW + 1;
+  constexpr bool IN_PLACE = STAGED && ONE_VIEW;
+  __shared__ float s_sh[STAGED ? 4 * 32 * RP : 1];
+  __shared__ float s_dsh[IN_PLACE ? 1 : 4 * 32 * RP];
+  const int64_t n = P.n;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float *wsh = s_sh + (STAGED ? wib * 32 * RP : 0);
+  float *dsh_row = IN_PLACE ? wsh + lane * RP : s_dsh + (wib * 32 + lane) * RP;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = base + threadIdx.x;
+    const int64_t g0 = base + wib * 32;
+    const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
+    if (STAGED) {
+      const float *src = P.sh + g0 * RW;
+      for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
+      __syncwarp();
+    }
+    if (g < n) {
+      const float *sh = STAGED ? wsh + lane * RP : P.sh + (int64_t)g * P.sh_stride * 3;
+      if (!IN_PLACE) {
+#pragma unroll
+        for (int k = 0; k < RW; ++k) dsh_row[k] = 0.f;
+      }
+      const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
+      float dm0 = 0.f, dm1 = 0.f, dm2 = 0.f;
+      bool any = false;
+      for (int v = 0; v < n_views; ++v) {
+        const int64_t r = (int64_t)v * n + g;
+        if (proj.radius[r] <= 0) continue;
+        any = true;
+        const gs_camera_t &cam = cams[v];
+        const float4 grgb = reinterpret_cast<const float4 *>(rg.d_rgb)[r];
+        const uint8_t cl = proj.clamped[r];
+        const float g0c = (cl & 1) ? 0.f : grgb.x, g1c = (cl & 2) ? 0.f : grgb.y, g2c = (cl & 4) ? 0.f : grgb.z;
+        float ccx, ccy, ccz;
+        camera_centre(cam, ccx, ccy, ccz);
+        const float ex = mx - ccx, ey = my - ccy, ez = mz - ccz;
+        const float il = rsqrtf(ex * ex + ey * ey + ez * ez);
+        const float dxn = ex * il, dyn = ey * il, dzn = ez * il;
+        float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+        sh_visit<DEG>(dxn, dyn, dzn, [&](int k, float Y, float yx, float yy, float yz) {
+          const float wk = g0c * sh[3 * k + 0] + g1c * sh[3 * k + 1] + g2c * sh[3 * k + 2];
+          if (IN_PLACE) {
+            dsh_row[3 * k + 0] = g0c * Y;
+            dsh_row[3 * k + 1] = g1c * Y;
+            dsh_row[3 * k + 2] = g2c * Y;
+          } else {
+            dsh_row[3 * k + 0] += g0c * Y;
+            dsh_row[3 * k + 1] += g1c * Y;
+            dsh_row[3 * k + 2] += g2c * Y;
+          }
+          gdx = fmaf(wk, yx, gdx);
+          gdy = fmaf(wk, yy, gdy);
+          gdz = fmaf(wk, yz, gdz);
+        });
+        // dir = (mu - centre) / |mu - centre|
+        const float dd = gdx * dxn + gdy * dyn + gdz * dzn;
+        dm0 += (gdx - dd * dxn) * il;
+        dm1 += (gdy - dd * dyn) * il;
+        dm2 += (gdz - dd * dzn) * il;
+      }
+      if (any) {
+        out.d_means[3 * g + 0] += dm0;
+        out.d_means[3 * g + 1] += dm1;
+        out.d_means[3 * g + 2] += dm2;
+      } else if (IN_PLACE) {
+#pragma unroll
+        for (int k = 0; k < RW; ++k) dsh_row[k] = 0.f;   // culled: zero gradient
+      }
+      if (!STAGED) {
+        float *dsh = out.d_sh + (int64_t)g * P.sh_stride * 3;
+#pragma unroll
+        for (int k = 0; k < RW; ++k) dsh[k] = dsh_row[k];
+        for (int k = K; k < P.sh_stride; ++k) dsh[3 * k + 0] = dsh[3 * k + 1] = dsh[3 * k + 2] = 0.f;
+      }
+    }
     if (STAGED) {
       __syncwarp();
       float *dst = out.d_sh + g0 * RW;
-      for (int f = lane; f < rows * RW; f += 32) dst[f] = wsh[(f / RW) * RP + (f % RW)];
+      const float *srow = IN_PLACE ? wsh : s_dsh + wib * 32 * RP;
+      for (int f = lane; f < rows * RW; f += 32) dst[f] = srow[(f / RW) * RP + (f % RW)];
       __syncwarp();
     }
   }
@@ -492,7 +493,12 @@ __global__ void densify_accum_kernel(const float *__restrict__ d_mean2d, const i
 template <int DEG, bool STAGED>
 static void launch_bwd_k(int grid, cudaStream_t s, const gs_params_t &P, const gs_frame_t *frame, const gs_proj_t &proj,
                          const gs_rec_grads_t &rg, const gs_param_grads_t &out, float *acc, int32_t *cnt) {
-  project_bwd_kernel<DEG, STAGED><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
+  project_bwd_geom_kernel<<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
+  count_launch();
+  if (frame->n_views == 1)
+    project_bwd_sh_kernel<DEG, STAGED, true><<<grid, 128, 0, s>>>(P, frame->cams_dev, 1, proj, rg, out);
+  else
+    project_bwd_sh_kernel<DEG, STAGED, false><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out);
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
