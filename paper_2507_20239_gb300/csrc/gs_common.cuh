@@ -67,17 +67,19 @@ struct Falloff {
 };
 
 // The quadratic form is non-negative by construction (A, gamma > 0), so no entry
-// needs the "exponent > 0" rejection; G = 2^(q * (-1/2 log2 e)).
+// needs the "exponent > 0" rejection. The kernels stage the conic pre-scaled,
+// a2 = k A and g2 = k gamma with k = -1/2 log2 e, so that G = 2^(a2 t^2 + g2 dy^2)
+// with t = dx + beta dy; d = mean - pixel centre.
 constexpr float kNegHalfLog2e = -0.72134752044448170f;
 
-__device__ __forceinline__ Falloff falloff(float u, float v, float A, float beta, float gamma, float o,
+__device__ __forceinline__ Falloff falloff(float u, float v, float a2, float beta, float g2, float o,
                                            float px, float py) {
   Falloff f;
   f.dx = __fsub_rn(u, px);
   f.dy = __fsub_rn(v, py);
   f.t = __fmaf_rn(beta, f.dy, f.dx);
-  const float q = __fmaf_rn(__fmul_rn(A, f.t), f.t, __fmul_rn(gamma, __fmul_rn(f.dy, f.dy)));
-  f.G = ex2_approx(__fmul_rn(q, kNegHalfLog2e));
+  const float e = __fmaf_rn(__fmul_rn(a2, f.t), f.t, __fmul_rn(g2, __fmul_rn(f.dy, f.dy)));
+  f.G = ex2_approx(e);
   f.raw = __fmul_rn(o, f.G);
   f.alpha = fminf(kAlphaMax, f.raw);
   return f;

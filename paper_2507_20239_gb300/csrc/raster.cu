@@ -46,36 +46,38 @@ __device__ __forceinline__ void pixel_of(int t, int &lx, int &ly) {
   ly = (w / (TW / 8)) * 8 + (l >> 2);
 }
 
-// Stage list entry r: position, factored conic + opacity, colour; colour.w holds the
-// mask of the tile's 8x8 blocks whose pixel centres the footprint ellipse meets (the
-// binning's conservative test), so a warp can skip records that miss its block.
-template <int TW, int TH>
+// Stage list entry r: position, pre-scaled conic (k A, beta, k gamma, o) with
+// k = -1/2 log2 e, colour; colour.w holds the mask of the tile's BW x BH blocks
+// (one per warp) whose pixel centres the footprint ellipse meets (the binning's
+// conservative test), so a warp can skip records that miss its block. co_raw
+// returns the unscaled (A, beta, gamma, o).
+template <int TW, int TH, int BW, int BH>
 __device__ __forceinline__ void stage(const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
                                       const float4 *__restrict__ rgb, uint32_t r, int x0, int y0, int W, int H,
-                                      float2 &xy, float4 &co, float4 &c) {
+                                      float2 &xy, float4 &co, float4 &c, float4 &co_raw) {
+  constexpr int NB = (TW / BW) * (TH / BH);
   xy = mean2d[r];
-  co = conic_o[r];
+  co_raw = conic_o[r];
   c = rgb[r];
   uint32_t m = 1u;
-  if (TW * TH > 64) {
+  if (NB > 1) {
     float ab, inv_den;
-    tile_hit_consts(co.x, co.y, co.z, ab, inv_den);
+    tile_hit_consts(co_raw.x, co_raw.y, co_raw.z, ab, inv_den);
     const float qb = __fmul_rn(c.w, kBinMargin);
     m = 0u;
 #pragma unroll
-    for (int b = 0; b < TW * TH / 64; ++b) {
-      const int bx = x0 + (b % (TW / 8)) * 8, by = y0 + (b / (TW / 8)) * 8;
+    for (int b = 0; b < NB; ++b) {
+      const int bx = x0 + (b % (TW / BW)) * BW, by = y0 + (b / (TW / BW)) * BH;
       if (bx >= W || by >= H) continue;
-      const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + 8, W) - 0.5f;
-      const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + 8, H) - 0.5f;
-      if (tile_hit(xy.x, xy.y, co.x, co.y, co.z, ab, inv_den, qb, X0, X1, Y0, Y1)) m |= 1u << b;
+      const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + BW, W) - 0.5f;
+      const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + BH, H) - 0.5f;
+      if (tile_hit(xy.x, xy.y, co_raw.x, co_raw.y, co_raw.z, ab, inv_den, qb, X0, X1, Y0, Y1)) m |= 1u << b;
     }
   }
+  co = make_float4(__fmul_rn(co_raw.x, kNegHalfLog2e), co_raw.y, __fmul_rn(co_raw.z, kNegHalfLog2e), co_raw.w);
   c.w = __uint_as_float(m);
 }
 
-// COUNT: instead of the image, write per pixel (entries examined up to and including
-// the one that triggers the cut-off, entries composited) to counts[2 * pixel].
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
@@ -103,9 +105,11 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
   const int n = (int)(rg.y - rg.x);
   for (int base = 0; base < n; base += NT) {
     if (__syncthreads_count(!(done0 && done1)) == 0) break;
-    if (base + t < n)
-      stage<TW, TH>(mean2d, conic_o, rgb, vals[rg.x + base + t], tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t],
-                    s_rgb[t]);
+    if (base + t < n) {
+      float4 co_raw;
+      stage<TW, TH, 8, 8>(mean2d, conic_o, rgb, vals[rg.x + base + t], tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t],
+                          s_co[t], s_rgb[t], co_raw);
+    }
     __syncthreads();
     if (__all_sync(0xffffffffu, done0 && done1)) continue;
     const int cnt = min(NT, n - base);
@@ -211,8 +215,12 @@ struct PixBwd {
   bool done;
 };
 
-// One pixel's contribution of the current Gaussian, accumulated into v[9] =
-// (d_u, d_v, d_A, d_beta, d_gamma, d_o, d_r, d_g, d_b); co = (A, beta, gamma, o).
+// One pixel's contribution of the current Gaussian. With m = dL/dalpha * G on
+// pixels where alpha is not clamped at 0.99, v[9] accumulates the moments
+// (sum m t, sum m dy, sum m t^2, sum m t dy, sum m dy^2, sum m) and the colour
+// gradient (sum d alpha T); the per-record epilogue turns the moments into the
+// gradients w.r.t. (u, v, A, beta, gamma, o) of the quadratic form
+// A (dx + beta dy)^2 + gamma dy^2 with dG/dq = -G/2. co = (k A, beta, k gamma, o).
 __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, const float4 co,
                                         const float4 c, float *v) {
   if (p.done) return false;
@@ -232,77 +240,84 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, co
   v[6] = fmaf(p.d0, w, v[6]);
   v[7] = fmaf(p.d1, w, v[7]);
   v[8] = fmaf(p.d2, w, v[8]);
-  if (f.raw <= kAlphaMax) {
-    v[5] = fmaf(f.G, dLda, v[5]);
-    // P = -1/2 (A t^2 + gamma dy^2), t = dx + beta dy, dx = u - p_x, dy = v - p_y
-    const float dP = dLda * f.raw;
-    const float At = co.x * f.t, gdy = co.z * f.dy;
-    const float hP = -0.5f * dP;
-    v[0] = fmaf(-dP, At, v[0]);
-    v[1] = fmaf(-dP, fmaf(At, co.y, gdy), v[1]);
-    v[2] = fmaf(hP * f.t, f.t, v[2]);
-    v[3] = fmaf(-dP * At, f.dy, v[3]);
-    v[4] = fmaf(hP * f.dy, f.dy, v[4]);
-  }
+  const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
+  const float mt = m * f.t, mdy = m * f.dy;
+  v[0] += mt;
+  v[1] += mdy;
+  v[2] = fmaf(mt, f.t, v[2]);
+  v[3] = fmaf(mt, f.dy, v[3]);
+  v[4] = fmaf(mdy, f.dy, v[4]);
+  v[5] += m;
   return true;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
+// PX pixels per thread: lane l of warp w owns the 2 x (PX/2) block at column
+// 2 (l % 4), row (PX/2) (l / 4) of the warp's 8 x 4PX block, so the per-entry
+// overhead and the warp reduction are shared by PX pixels.
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image, float *__restrict__ g_mean2d,
     float *__restrict__ g_co, float *__restrict__ g_rgb) {
-  constexpr int NT = TW * TH / 2;
+  constexpr int NT = TW * TH / PX, BW = 8, BH = 4 * PX;
   __shared__ float2 s_xy[NT];
   __shared__ float4 s_co[NT];
   __shared__ float4 s_rgb[NT];
   __shared__ uint32_t s_rec[NT];
+  __shared__ float4 s_cu[NT];
   __shared__ float s_acc[NT * 9];
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  int lx, ly;
-  pixel_of<TW>(t, lx, ly);
-  const int py = tc.ty * TH + ly;
-  const int px = tc.tx * TW + lx;
-  const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
-  const float fy = (float)py + 0.5f;
+  const int lx = (warp % (TW / BW)) * BW + 2 * (lane & 3);
+  const int ly = (warp / (TW / BW)) * BH + (PX / 2) * (lane >> 2);
   const int64_t plane = (int64_t)tc.W * tc.H;
-  const int64_t p0 = (int64_t)py * tc.W + px;
   const float *img = image + 3 * tc.pix_off;
   const float *dim = d_image + 3 * tc.pix_off;
-  PixBwd q0{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in0};
-  PixBwd q1{(float)px + 1.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in1};
-  if (in0) {
-    q0.d0 = dim[p0]; q0.d1 = dim[plane + p0]; q0.d2 = dim[2 * plane + p0];
-    q0.K = q0.d0 * img[p0] + q0.d1 * img[plane + p0] + q0.d2 * img[2 * plane + p0];
+  PixBwd q[PX];
+  float fy[PX / 2];
+#pragma unroll
+  for (int k = 0; k < PX; ++k) {
+    const int px = tc.tx * TW + lx + (k & 1), py = tc.ty * TH + ly + (k >> 1);
+    const bool in = py < tc.H && px < tc.W;
+    q[k] = PixBwd{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in};
+    if ((k & 1) == 0) fy[k >> 1] = (float)py + 0.5f;
+    if (in) {
+      const int64_t p = (int64_t)py * tc.W + px;
+      q[k].d0 = dim[p]; q[k].d1 = dim[plane + p]; q[k].d2 = dim[2 * plane + p];
+      q[k].K = q[k].d0 * img[p] + q[k].d1 * img[plane + p] + q[k].d2 * img[2 * plane + p];
+    }
   }
-  if (in1) {
-    q1.d0 = dim[p0 + 1]; q1.d1 = dim[plane + p0 + 1]; q1.d2 = dim[2 * plane + p0 + 1];
-    q1.K = q1.d0 * img[p0 + 1] + q1.d1 * img[plane + p0 + 1] + q1.d2 * img[2 * plane + p0 + 1];
-  }
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) d = d && q[k].done;
+    return d;
+  };
   const uint2 rg = ranges[blockIdx.x];
   const int n = (int)(rg.y - rg.x);
   for (int base = 0; base < n; base += NT) {
-    if (__syncthreads_count(!(q0.done && q1.done)) == 0) break;
+    if (__syncthreads_count(!all_done()) == 0) break;
     const int cnt = min(NT, n - base);
     if (t < cnt) {
       const uint32_t r = vals[rg.x + base + t];
       s_rec[t] = r;
-      stage<TW, TH>(mean2d, conic_o, rgb, r, tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t], s_rgb[t]);
+      stage<TW, TH, BW, BH>(mean2d, conic_o, rgb, r, tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t], s_rgb[t],
+                            s_cu[t]);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) s_acc[k * NT + t] = 0.f;
     __syncthreads();
-    if (!__all_sync(0xffffffffu, q0.done && q1.done)) {
+    if (!__all_sync(0xffffffffu, all_done())) {
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int j = 0; j < cnt; ++j) {
         const float4 c = s_rgb[j];
         if (!((__float_as_uint(c.w) >> warp) & 1u)) continue;   // warp-uniform skip
         const float2 xy = s_xy[j];
         const float4 co = s_co[j];
-        bool any = pix_bwd(q0, fy, xy, co, c, v);
-        any |= pix_bwd(q1, fy, xy, co, c, v);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) any |= pix_bwd(q[k], fy[k >> 1], xy, co, c, v);
         if (__any_sync(0xffffffffu, any)) {
           warp_reduce9_add(v, s_acc + j * 9, lane);
 #pragma unroll
@@ -313,12 +328,15 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_bwd_kernel(
     __syncthreads();
     if (t < cnt) {
       const float *a = s_acc + t * 9;
-      const float u0 = a[0], u1 = a[1], c0 = a[2], c1 = a[3], c2 = a[4], c3 = a[5], k0 = a[6], k1 = a[7], k2 = a[8];
-      if (u0 != 0.f || u1 != 0.f || c0 != 0.f || c1 != 0.f || c2 != 0.f || c3 != 0.f || k0 != 0.f || k1 != 0.f ||
-          k2 != 0.f) {
+      const float mt = a[0], mdy = a[1], mtt = a[2], mtdy = a[3], mdydy = a[4], m = a[5];
+      const float k0 = a[6], k1 = a[7], k2 = a[8];
+      if (mt != 0.f || mdy != 0.f || mtt != 0.f || mtdy != 0.f || mdydy != 0.f || m != 0.f || k0 != 0.f ||
+          k1 != 0.f || k2 != 0.f) {
         const uint32_t r = s_rec[t];
-        red_add_v2(g_mean2d + 2 * (size_t)r, u0, u1);
-        red_add_v4(g_co + 4 * (size_t)r, c0, c1, c2, c3);
+        const float4 cu = s_cu[t];   // (A, beta, gamma, o)
+        const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
+        red_add_v2(g_mean2d + 2 * (size_t)r, -oA * mt, -(oA * cu.y * mt + cu.w * cu.z * mdy));
+        red_add_v4(g_co + 4 * (size_t)r, ho * mtt, -oA * mtdy, ho * mdydy, m);
         red_add_v4(g_rgb + 4 * (size_t)r, k0, k1, k2, 0.f);
       }
     }
@@ -370,7 +388,10 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
-  raster_bwd_kernel<TW, TH><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
+  // 2 pixels per thread: 8 x 8 warp blocks skip more records than 8 x 16 ones
+  // (4 pixels per thread) save in shared per-entry work.
+  constexpr int PX = 2;
+  raster_bwd_kernel<TW, TH, PX><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, image, d_image, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
