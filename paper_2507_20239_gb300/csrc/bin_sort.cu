@@ -11,9 +11,14 @@
 // the order is built in two stable stages that give the same permutation:
 //   1. the visible records (one entry each) are compacted in record order and
 //      sorted by their 32-bit depth key (stable LSD radix sort, 4 x 8-bit passes);
-//   2. every record, taken in depth order, emits one entry per tile of its
-//      rectangle, and the entries are stably sorted by tile id alone (ceil(bits/8)
-//      passes of <= 8 bits).
+//   2. every record, taken in depth order, emits one entry per tile its footprint
+//      meets, and the entries are stably sorted by tile id alone. The first LSD
+//      digit of that sort (the low FB bits of the tile id) is fused into the
+//      emission: a counting pass histograms each warp batch's hits by that digit,
+//      a scan turns the (digit, batch) counts into cursors, and the emitting pass
+//      writes every entry straight to its digit-partitioned position. The remaining
+//      high bits take ceil((bits - FB) / 8) ordinary passes (none when the tile id
+//      has at most 8 bits).
 // A stable sort by tile of a depth-ordered sequence is ordered by (tile, depth,
 // record). Stage 2 moves 8 bytes per duplicate per pass instead of 12 bytes per
 // pass for 5-6 passes.
@@ -89,12 +94,19 @@ __global__ void __launch_bounds__(32) rs_scan_kernel(uint32_t *hist, int G, uint
 }
 
 // Stable scatter. Each warp ranks a contiguous slice of the tile, 32 keys per
-// step in order, with __match_any_sync; slices are then offset by the warps before
-// them, staged in shared memory in digit order and written out coalesced.
+// step in order; slices are then offset by the warps before them, staged in shared
+// memory in digit order and written out coalesced. Ranking within a step: for
+// digits of NB <= 6 bits (BITS = NB), the peers of a key are the AND of NB
+// ballots (one per digit bit) and lane l keeps the running counts of digits l and
+// l + 32 in registers; wider digits (BITS = 0) use __match_any_sync and a per-warp
+// shared-memory count.
+template <int BITS>
 __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *d_n, const uint32_t *d_skip, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
+  static_assert(BITS >= 0 && BITS <= 6, "ballot ranking covers digits of at most 6 bits");
+  constexpr int kSlots = BITS == 0 ? 0 : ((1 << BITS) + 31) / 32;
   __shared__ uint32_t s_keys[kRsTile];
   __shared__ uint32_t s_vals[kRsTile];
   __shared__ uint32_t s_whist[kRsWarps][kRsBins + 1];
@@ -112,11 +124,16 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     const uint32_t dbase = block_exclusive_scan<uint32_t>(totals[threadIdx.x], &all);
     s_goff[threadIdx.x] = dbase + hist[(uint64_t)threadIdx.x * G + blockIdx.x];
   }
+  if (BITS > 0) {   // digits >= 2^BITS never occur: zero once
+    for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
+  }
   const uint32_t lt_mask = lanemask_lt();
   for (uint64_t tb = begin; tb < end; tb += kRsTile) {
     const uint32_t tile_n = (uint32_t)min((uint64_t)kRsTile, end - tb);
-    for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
-    __syncwarp();
+    if (BITS == 0) {
+      for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
+      __syncwarp();
+    }
     uint32_t k[kRsItems], v[kRsItems], dig[kRsItems], rank[kRsItems];
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
@@ -126,15 +143,50 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
       v[j] = valid ? vals_in[tb + li] : 0u;
       dig[j] = valid ? ((k[j] >> shift) & mask) : (uint32_t)kRsBins;
     }
+    if (BITS == 0) {
 #pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
-      const uint32_t before = __popc(peers & lt_mask);
-      const uint32_t base = s_whist[warp][dig[j]];
-      __syncwarp();
-      rank[j] = base + before;
-      if (before == 0) s_whist[warp][dig[j]] = base + __popc(peers);
-      __syncwarp();
+      for (int j = 0; j < kRsItems; ++j) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+        const uint32_t before = __popc(peers & lt_mask);
+        const uint32_t base = s_whist[warp][dig[j]];
+        __syncwarp();
+        rank[j] = base + before;
+        if (before == 0) s_whist[warp][dig[j]] = base + __popc(peers);
+        __syncwarp();
+      }
+    } else {
+      uint32_t cnt[kSlots > 0 ? kSlots : 1];
+#pragma unroll
+      for (int q = 0; q < kSlots; ++q) cnt[q] = 0;
+#pragma unroll
+      for (int j = 0; j < kRsItems; ++j) {
+        const uint32_t d = dig[j];
+        const uint32_t vm = __ballot_sync(0xffffffffu, d < (uint32_t)kRsBins);
+        uint32_t mb[BITS > 0 ? BITS : 1];
+        uint32_t peers = vm;
+#pragma unroll
+        for (int b = 0; b < BITS; ++b) {
+          mb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+          peers &= ((d >> b) & 1u) ? mb[b] : ~mb[b];
+        }
+        uint32_t base = __shfl_sync(0xffffffffu, cnt[0], d & 31u);
+        if (kSlots > 1) {
+          const uint32_t hi = __shfl_sync(0xffffffffu, cnt[kSlots > 1 ? 1 : 0], d & 31u);
+          base = ((d >> 5) & 1u) ? hi : base;
+        }
+        rank[j] = base + __popc(peers & lt_mask);
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+          const uint32_t own = lane + 32u * q;   // digit whose count this lane keeps
+          uint32_t m = vm;
+#pragma unroll
+          for (int b = 0; b < BITS; ++b) m &= ((own >> b) & 1u) ? mb[b] : ~mb[b];
+          if (own < (1u << BITS)) cnt[q] += __popc(m);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kSlots; ++q)
+        if (lane + 32 * q < (1 << BITS)) s_whist[warp][lane + 32 * q] = cnt[q];
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -155,6 +207,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
+      if (BITS > 0 && dig[j] >= (uint32_t)kRsBins) continue;   // not counted: past the tile's end
       const uint32_t pos = s_tstart[dig[j]] + s_whist[warp][dig[j]] + rank[j];
       s_keys[pos] = k[j];
       s_vals[pos] = v[j];
@@ -190,19 +243,23 @@ struct VisibleCompact {
   __device__ void total(uint64_t t) const { *n_vis = (uint32_t)t; }
 };
 
-struct TouchedOffsets {
-  const uint32_t *counts;     // tiles hit by each depth-ordered record
+// Exclusive scan, in place, of the (digit, batch) hit counts stored digit-major
+// (hist[d * NB + b], NB = number of 32-record batches): the result is each batch's
+// first output position for each digit. The total is M; above the duplicate
+// capacity the frame overflows.
+struct HistScan {
+  uint32_t *hist;
   const uint32_t *n_vis;
-  uint32_t *offsets;
+  int fbits;
   uint64_t capacity;
   uint32_t *m_total;          // M (0 on overflow)
   uint32_t *overflow;
   int64_t *d_count;
   int32_t *d_error;
-  __device__ uint64_t count() const { return *n_vis; }
-  __device__ uint32_t value(uint64_t k) const { return counts[k]; }
-  __device__ void emit(uint64_t k, uint64_t pre, uint32_t) const {
-    if (pre <= 0xffffffffull) offsets[k] = (uint32_t)pre;
+  __device__ uint64_t count() const { return ((uint64_t)(*n_vis) + 31u) / 32u << fbits; }
+  __device__ uint32_t value(uint64_t i) const { return hist[i]; }
+  __device__ void emit(uint64_t i, uint64_t pre, uint32_t) const {
+    if (pre <= 0xffffffffull) hist[i] = (uint32_t)pre;
   }
   __device__ void total(uint64_t t) const {
     *d_count = (int64_t)t;
@@ -249,34 +306,39 @@ __device__ __forceinline__ bool candidate(const RecordTiles &t, uint32_t c, int 
 }
 
 // Warp-cooperative pass over the candidate tiles of 32 depth-ordered records at a
-// time: lane l loads record k0 + l (one round of independent loads), the 32
-// candidate lists are concatenated by a warp scan, and each lane then takes one
-// candidate per step, finding its record by a binary search over the scan and
-// reading that record's fields with shuffles. COUNT writes the hits per record;
-// EMIT writes (tile id, record) for every hit at the record's offset, in candidate
-// order.
+// time (one batch): lane l loads record k0 + l (one round of independent loads),
+// the 32 candidate lists are concatenated by a warp scan, and each lane then takes
+// one candidate per step, finding its record by a binary search over the scan and
+// reading that record's fields with shuffles. Hits are kept in candidate order per
+// digit d = tile & (2^fbits - 1): the count pass (EMIT = false) writes the batch's
+// hits per digit to hist[d * NB + batch]; the emitting pass starts each digit's
+// cursor at the scanned hist entry and writes (tile id, record) at the cursor.
+constexpr int kMaxFusedBits = 8;
+
 template <bool EMIT>
 __global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint32_t *__restrict__ order,
                                                          const uint32_t *n_vis, const uint32_t *overflow,
                                                          const gs_camera_t *__restrict__ cams, int n_views,
-                                                         int64_t n_per_view, int tw, int th,
-                                                         uint32_t *__restrict__ counts,
-                                                         const uint32_t *__restrict__ offsets,
-                                                         uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
-  __shared__ uint32_t s_run[8][32];   // hits so far per record of the warp's batch
+                                                         int64_t n_per_view, int tw, int th, int fbits,
+                                                         uint32_t *__restrict__ hist, uint32_t *__restrict__ dkeys,
+                                                         uint32_t *__restrict__ dvals) {
+  __shared__ uint32_t s_cur[8][1 << kMaxFusedBits];   // per warp: hits (count) / next position (emit) per digit
   if (EMIT && *overflow) return;
   const uint32_t nv = *n_vis;
+  const uint32_t NB = (nv + 31u) / 32u;
+  const uint32_t nd = 1u << fbits, dmask = nd - 1u;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < nv; k0 += nw * 32) {
+    const uint32_t batch = k0 / 32u;
+    for (uint32_t d = lane; d < nd; d += 32) s_cur[wib][d] = EMIT ? hist[(uint64_t)d * NB + batch] : 0u;
     const uint32_t k = k0 + lane;
     RecordTiles t{};
-    uint32_t r = 0, out0 = 0;
+    uint32_t r = 0;
     if (k < nv) {
       r = order[k];
       t = record_tiles(P, cams, n_views, n_per_view, r);
-      if (EMIT) out0 = offsets[k];
     }
     uint32_t incl = t.n;
 #pragma unroll
@@ -286,7 +348,6 @@ __global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint
     }
     const uint32_t excl = incl - t.n;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    s_run[wib][lane] = 0;
     __syncwarp();
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
       const uint32_t g = c0 + lane;
@@ -317,23 +378,25 @@ __global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint
       const uint32_t c = g - __shfl_sync(0xffffffffu, excl, j);
       uint32_t tile = 0;
       const bool hit = g < total && candidate(o, c, tw, th, tile);
-      const uint32_t same = __match_any_sync(0xffffffffu, (uint32_t)j);
-      const uint32_t hits = __ballot_sync(0xffffffffu, hit) & same;
-      if (EMIT) {
-        const uint32_t base_j = __shfl_sync(0xffffffffu, out0, j);
-        const uint32_t r_j = __shfl_sync(0xffffffffu, r, j);
-        if (hit) {
-          const uint32_t pos = base_j + s_run[wib][j] + __popc(hits & lt);
+      const uint32_t dig = tile & dmask;
+      // hits of this step with the same digit, in lane (= candidate) order
+      const uint32_t peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
+      const uint32_t r_j = EMIT ? __shfl_sync(0xffffffffu, r, j) : 0u;
+      uint32_t cur = 0;
+      if (hit) cur = s_cur[wib][dig];
+      __syncwarp();
+      if (hit) {
+        if (EMIT) {
+          const uint32_t pos = cur + __popc(peers & lt);
           dkeys[pos] = tile;
           dvals[pos] = r_j;
         }
+        if ((peers & lt) == 0) s_cur[wib][dig] = cur + __popc(peers);
       }
       __syncwarp();
-      // the lowest lane of each owner group advances that record's running count
-      if ((same & lt) == 0) s_run[wib][j] += __popc(hits);
-      __syncwarp();
     }
-    if (!EMIT && k < nv) counts[k] = s_run[wib][lane];
+    if (!EMIT)
+      for (uint32_t d = lane; d < nd; d += 32) hist[(uint64_t)d * NB + batch] = s_cur[wib][d];
     __syncwarp();
   }
 }
@@ -368,8 +431,7 @@ __global__ void keys64_kernel(const uint32_t *__restrict__ tiles, const uint32_t
 // ------------------------------------------------------------------ host side
 struct BinWs {
   uint32_t *vk0, *vv0, *vk1, *vv1;   // visible records: depth keys / record ids (double buffered)
-  uint32_t *counts;                  // tiles hit per depth-ordered record
-  uint32_t *offsets;                 // duplicate offsets in depth order
+  uint32_t *dhist;                   // (digit, batch) hit counts -> emission cursors
   uint32_t *dk0, *dk1, *dv1;         // duplicate tile keys (double buffered) + second value buffer
   uint64_t *block_sums;
   uint32_t *hist;
@@ -379,7 +441,7 @@ struct BinWs {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
+static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap, int fbits) {
   BinWs w{};
   char *p = static_cast<char *>(base);
   size_t off = 0;
@@ -392,8 +454,7 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap) {
   w.vv0 = (uint32_t *)take(4 * (size_t)R + 16);
   w.vk1 = (uint32_t *)take(4 * (size_t)R + 16);
   w.vv1 = (uint32_t *)take(4 * (size_t)R + 16);
-  w.counts = (uint32_t *)take(4 * (size_t)R + 16);
-  w.offsets = (uint32_t *)take(4 * (size_t)R + 16);
+  w.dhist = (uint32_t *)take(4 * ((((size_t)R + 31) / 32) << fbits) + 16);
   w.dk0 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dv1 = (uint32_t *)take(4 * (size_t)cap + 16);
@@ -411,17 +472,18 @@ static int radix_blocks() {
   return g > kMaxBlocks ? kMaxBlocks : g;
 }
 
-// Stable LSD radix sort of (key, val) pairs on bits [0, n_bits), ping-ponging between
+// Stable LSD radix sort of (key, val) pairs on bits [first_bit, n_bits), ping-ponging between
 // buffer 0 and 1; returns in *in_b0 whether the result is in buffer 0.
 static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *d_n,
-                              const uint32_t *d_skip, int n_bits, bool keep_keys, uint32_t *hist, int G,
+                              const uint32_t *d_skip, int first_bit, int n_bits, bool keep_keys, uint32_t *hist,
                               cudaStream_t s, bool *in_b0) {
-  G = radix_blocks();
-  const int passes = (n_bits + 7) / 8;
-  const int bits = (n_bits + passes - 1) / passes;
+  const int G = radix_blocks();
+  const int span = n_bits - first_bit;
+  const int passes = span > 0 ? (span + 7) / 8 : 0;
+  const int bits = passes > 0 ? (span + passes - 1) / passes : 0;
   bool cur0 = true;
   for (int p = 0; p < passes; ++p) {
-    const int shift = p * bits;
+    const int shift = first_bit + p * bits;
     const int nb = (shift + bits > n_bits) ? n_bits - shift : bits;
     const uint32_t mask = (1u << nb) - 1u;
     uint32_t *ki = cur0 ? k0 : k1, *vi = cur0 ? v0 : v1, *ko = cur0 ? k1 : k0, *vo = cur0 ? v1 : v0;
@@ -430,8 +492,18 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     rs_scan_kernel<<<kRsBins, 32, 0, s>>>(hist, G, hist + (size_t)kRsBins * kMaxBlocks, d_skip);
     GS_LAUNCH_CHECK();
     const bool last = p == passes - 1;
-    rs_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, (last && !keep_keys) ? nullptr : ko, vo, d_n, d_skip,
-                                                 shift, mask, hist, hist + (size_t)kRsBins * kMaxBlocks);
+    uint32_t *kout = (last && !keep_keys) ? nullptr : ko;
+    const uint32_t *tot = hist + (size_t)kRsBins * kMaxBlocks;
+    switch (nb) {
+#define GS_RS_DOWN(B)                                                                                          \
+  case B:                                                                                                      \
+    rs_downsweep_kernel<B><<<G, kRsThreads, 0, s>>>(ki, vi, kout, vo, d_n, d_skip, shift, mask, hist, tot); \
+    break;
+      GS_RS_DOWN(1) GS_RS_DOWN(2) GS_RS_DOWN(3) GS_RS_DOWN(4) GS_RS_DOWN(5) GS_RS_DOWN(6)
+#undef GS_RS_DOWN
+      default:
+        rs_downsweep_kernel<0><<<G, kRsThreads, 0, s>>>(ki, vi, kout, vo, d_n, d_skip, shift, mask, hist, tot);
+    }
     GS_LAUNCH_CHECK();
     cur0 = !cur0;
   }
@@ -445,14 +517,29 @@ static int bits_for(uint32_t max_value) {
   return b;
 }
 
+// Tile-id bits and the low digit fused into the emission: every bit above it is
+// covered by ceil((bits - fbits) / 8) radix passes, with fbits as small as that
+// pass count allows (a smaller digit means a smaller (digit, batch) histogram).
+static void tile_sort_plan(int n_tiles, int &tile_bits, int &fbits) {
+  tile_bits = bits_for((uint32_t)(n_tiles > 0 ? n_tiles - 1 : 0));
+  if (tile_bits <= kMaxFusedBits) {
+    fbits = tile_bits;
+    return;
+  }
+  const int passes = (tile_bits - kMaxFusedBits + 7) / 8;
+  fbits = tile_bits - 8 * passes;
+  if (fbits < 1) fbits = 1;
+}
+
 }  // namespace gs
 
 using namespace gs;
 
 extern "C" size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const gs_frame_t *frame) {
-  (void)frame;
   if (n_records < 0 || dup_capacity < 0) return 0;
-  return bin_ws_layout(nullptr, n_records, dup_capacity).bytes;
+  int tile_bits = 32, fbits = kMaxFusedBits;
+  if (frame) tile_sort_plan(frame->n_tiles, tile_bits, fbits);
+  return bin_ws_layout(nullptr, n_records, dup_capacity, fbits).bytes;
 }
 
 extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *frame, gs_bins_t *bins, void *ws,
@@ -464,7 +551,9 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int64_t R = proj->n_records;
   if (R < 0 || R >= (1ll << 31) || R % frame->n_views != 0) return GS_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GS_ERR_INVALID_ARG;
-  const BinWs w = bin_ws_layout(ws, R, bins->capacity);
+  int tile_bits, fbits;
+  tile_sort_plan(frame->n_tiles, tile_bits, fbits);
+  const BinWs w = bin_ws_layout(ws, R, bins->capacity, fbits);
   if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   const int G = scan_blocks();
@@ -476,32 +565,36 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   if (gs_status_t st = run_scan(vc, w.block_sums, G, s)) return st;
   // 2. stable sort by depth
   bool in0 = true;
-  if (gs_status_t st = radix_sort(w.vk0, w.vv0, w.vk1, w.vv1, n_vis, nullptr, 32, false, w.hist, G, s, &in0)) return st;
+  if (gs_status_t st = radix_sort(w.vk0, w.vv0, w.vk1, w.vv1, n_vis, nullptr, 0, 32, false, w.hist, s, &in0))
+    return st;
   const uint32_t *order = in0 ? w.vv0 : w.vv1;
-  // 3. tiles hit per record, duplicate offsets in depth order, M and the capacity check
+  // 3. hits per (low tile digit, batch of 32 depth-ordered records), scanned into
+  //    emission cursors; M and the capacity check
   const int64_t n_per_view = R / frame->n_views;
   const int eg = num_sms() * 8;
   candidates_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
-                                              n_per_view, frame->tile_w, frame->tile_h, w.counts, nullptr,
-                                              nullptr, nullptr);
+                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, nullptr,
+                                              nullptr);
   GS_LAUNCH_CHECK();
-  TouchedOffsets to{w.counts, n_vis, w.offsets, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
-  if (gs_status_t st = run_scan(to, w.block_sums, G, s)) return st;
-  // 4. emit (tile, record) in depth order, into the buffer the tile sort ends in
-  const int tile_bits = bits_for((uint32_t)(frame->n_tiles - 1));
-  const int passes = (tile_bits + 7) / 8;
+  HistScan hs{w.dhist, n_vis, fbits, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
+  if (gs_status_t st = run_scan(hs, w.block_sums, G, s)) return st;
+  // 4. emit (tile, record) partitioned by the low digit, in depth order within it,
+  //    into the buffer the remaining passes end in
+  const int passes = (tile_bits - fbits + 7) / 8;
   uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
   const bool emit_to_A = (passes % 2) == 0;
   candidates_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
-                                             n_per_view, frame->tile_w, frame->tile_h, nullptr, w.offsets,
+                                             n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist,
                                              emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
   GS_LAUNCH_CHECK();
-  // 5. stable sort by tile id
+  // 5. stable sort by the remaining tile-id bits
   bool res0 = true;
   if (emit_to_A) {
-    if (gs_status_t st = radix_sort(A_k, A_v, B_k, B_v, m_total, overflow, tile_bits, true, w.hist, G, s, &res0)) return st;
+    if (gs_status_t st = radix_sort(A_k, A_v, B_k, B_v, m_total, overflow, fbits, tile_bits, true, w.hist, s, &res0))
+      return st;
   } else {
-    if (gs_status_t st = radix_sort(B_k, B_v, A_k, A_v, m_total, overflow, tile_bits, true, w.hist, G, s, &res0)) return st;
+    if (gs_status_t st = radix_sort(B_k, B_v, A_k, A_v, m_total, overflow, fbits, tile_bits, true, w.hist, s, &res0))
+      return st;
     res0 = !res0;
   }
   // 6. per-tile ranges (and optional 64-bit keys)

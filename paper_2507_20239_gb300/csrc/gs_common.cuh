@@ -127,6 +127,44 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, 
   return m <= qb;
 }
 
+// x-extent of the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb (d = mean - p) over
+// a band of pixel-centre rows Y0 <= y <= Y1. At fixed dy the ellipse spans
+// x = u + beta dy +- sqrt((qb - gamma dy^2) / A); the right end is concave in dy and
+// peaks at the rightmost point of the ellipse, dy_r = beta sqrt(qb A / (gamma (A beta^2
+// + gamma))), the left end bottoms out at -dy_r, so over the band each end is taken
+// at the clamped extreme. A box [X0, X1] x [Y0, Y1] meets the ellipse iff the band is
+// not empty and [X0, X1] meets [xl, xr]. Approximate (MUFU) square root and
+// reciprocal: callers use it as a conservative skip test with a margin in qb far
+// above their few-ulp error.
+struct EllipseRows {
+  float u, v, beta, gamma, inv_A, qb, dyr;
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ EllipseRows ellipse_rows(float u, float v, float A, float beta, float gamma, float qb) {
+  EllipseRows e;
+  e.u = u; e.v = v; e.beta = beta; e.gamma = gamma; e.qb = qb;
+  e.inv_A = __fdividef(1.f, A);
+  const float den = fmaf(A * beta, beta, gamma);
+  e.dyr = beta * sqrt_approx(__fdividef(qb * A, gamma * den));
+  return e;
+}
+
+__device__ __forceinline__ bool row_span(const EllipseRows &e, float Y0, float Y1, float &xl, float &xr) {
+  const float dyl = e.v - Y1, dyh = e.v - Y0;
+  const float dr = fminf(fmaxf(e.dyr, dyl), dyh), dl = fminf(fmaxf(-e.dyr, dyl), dyh);
+  const float wr = e.qb - e.gamma * dr * dr, wl = e.qb - e.gamma * dl * dl;
+  if (wr < 0.f && wl < 0.f) return false;
+  xr = fmaf(e.beta, dr, e.u) + sqrt_approx(fmaxf(wr, 0.f) * e.inv_A);
+  xl = fmaf(e.beta, dl, e.u) - sqrt_approx(fmaxf(wl, 0.f) * e.inv_A);
+  return true;
+}
+
 // Find the view owning global tile t (views are few; a linear scan of the cameras).
 __device__ __forceinline__ int view_of_tile(const gs_camera_t *cams, int n_views, int t) {
   int v = 0;

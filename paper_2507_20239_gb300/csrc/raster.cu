@@ -3,15 +3,17 @@
 // One CTA per tile, two horizontally adjacent pixels per thread; each warp owns an
 // 8x8 block of the tile. The tile's depth-ordered list is consumed in batches of one
 // record per thread, staged in shared memory together with a mask of the 8x8
-// blocks the record's footprint reaches (the binning's exact ellipse-box test), so a
-// warp skips the records that cannot touch its pixels. A pixel stops before the
+// blocks the record's footprint ellipse reaches (per 8-row band, the ellipse's
+// x-extent against the blocks' columns), so a warp skips the records that cannot
+// touch its pixels. A pixel stops before the
 // entry that would drive its transmittance below 1e-4 and the CTA leaves once every
 // pixel has stopped.
 //
 // The backward pass re-walks the list front to back with exactly the forward's
 // FP32 decisions (no stored stop index) and needs, per pixel, only <dL/dout, out>:
 //   dL/dsigma_i = T_i <c_i, g> - (<out, g> - sum_{j<=i} <c_j, g> sigma_j T_j) / (1 - sigma_i).
-// The 9 per-(pixel, Gaussian) gradient terms are summed over the thread's two
+// The 9 per-(pixel, Gaussian) terms (six moments of the falloff gradient, three
+// colour terms) are summed over the thread's two
 // pixels in registers, across the warp with a transposing shuffle reduction, across
 // the CTA's warps in shared memory, and then added once per (tile, record) to the
 // record gradients with vector reductions.
@@ -48,8 +50,8 @@ __device__ __forceinline__ void pixel_of(int t, int &lx, int &ly) {
 
 // Stage list entry r: position, pre-scaled conic (k A, beta, k gamma, o) with
 // k = -1/2 log2 e, colour; colour.w holds the mask of the tile's BW x BH blocks
-// (one per warp) whose pixel centres the footprint ellipse meets (the binning's
-// conservative test), so a warp can skip records that miss its block. co_raw
+// (one per warp) whose pixel centres the footprint ellipse (q <= q_max with the
+// binning's margin) meets, so a warp can skip records that miss its block. co_raw
 // returns the unscaled (A, beta, gamma, o).
 template <int TW, int TH, int BW, int BH>
 __device__ __forceinline__ void stage(const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o,
@@ -61,17 +63,18 @@ __device__ __forceinline__ void stage(const float2 *__restrict__ mean2d, const f
   c = rgb[r];
   uint32_t m = 1u;
   if (NB > 1) {
-    float ab, inv_den;
-    tile_hit_consts(co_raw.x, co_raw.y, co_raw.z, ab, inv_den);
-    const float qb = __fmul_rn(c.w, kBinMargin);
+    const EllipseRows e = ellipse_rows(xy.x, xy.y, co_raw.x, co_raw.y, co_raw.z, c.w * kBinMargin);
     m = 0u;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int bx = x0 + (b % (TW / BW)) * BW, by = y0 + (b / (TW / BW)) * BH;
-      if (bx >= W || by >= H) continue;
-      const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + BW, W) - 0.5f;
-      const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + BH, H) - 0.5f;
-      if (tile_hit(xy.x, xy.y, co_raw.x, co_raw.y, co_raw.z, ab, inv_den, qb, X0, X1, Y0, Y1)) m |= 1u << b;
+    for (int by = 0; by < TH / BH; ++by) {
+      const int yb = y0 + by * BH;
+      float xl, xr;
+      if (yb >= H || !row_span(e, (float)yb + 0.5f, (float)min(yb + BH, H) - 0.5f, xl, xr)) continue;
+#pragma unroll
+      for (int bx = 0; bx < TW / BW; ++bx) {
+        const int xb = x0 + bx * BW;
+        if (xb < W && (float)min(xb + BW, W) - 0.5f >= xl && (float)xb + 0.5f <= xr) m |= 1u << (by * (TW / BW) + bx);
+      }
     }
   }
   co = make_float4(__fmul_rn(co_raw.x, kNegHalfLog2e), co_raw.y, __fmul_rn(co_raw.z, kNegHalfLog2e), co_raw.w);
