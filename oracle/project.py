@@ -128,6 +128,47 @@ def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
     return inside | (m <= qb)
 
 
+def band_span(u, v, A, beta, gamma, qb, Y0, Y1):
+    """x-extent [xl, xr] of the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb,
+    d = mean - p, over the band of pixel centres Y0 <= y <= Y1.
+
+    At fixed dy the ellipse covers x = u + beta dy +- sqrt((qb - gamma dy^2) / A).
+    The right end is concave in dy with its maximum at the ellipse's rightmost
+    point, dy_r = beta sqrt(qb A / (gamma (A beta^2 + gamma))) (where the conic's
+    x-extreme dx = -(Sigma''_xx qb)^(1/2) sits, dy = -(B / C) dx), and the left end
+    is convex with its minimum at -dy_r; over the band each end is therefore taken
+    at the extreme clamped into [v - Y1, v - Y0]. A box [X0, X1] x [Y0, Y1] meets the
+    ellipse exactly when ok and X1 >= xl and X0 <= xr and xl <= xr (band_hit).
+
+    Elementwise in the inputs' dtype, one rounded operation each (the CUDA binning
+    evaluates the same sequence, with dy_r and 1/A formed once per record);
+    fmax/fmin ignore a NaN operand like C's.
+    Returns (ok, xl, xr); ok is False where the band misses the ellipse.
+    """
+    dt = np.result_type(u, A)
+    zero = dt.type(0)
+    ab = A * beta
+    den = ab * beta + gamma
+    dyr = beta * np.sqrt((qb * A) / (gamma * den))
+    inv_A = dt.type(1) / A
+    dyl, dyh = v - Y1, v - Y0
+    dr = np.fmin(np.fmax(dyr, dyl), dyh)
+    dl = np.fmin(np.fmax(-dyr, dyl), dyh)
+    wr = qb - gamma * (dr * dr)
+    wl = qb - gamma * (dl * dl)
+    ok = (wr >= zero) | (wl >= zero)
+    xr = (u + beta * dr) + np.sqrt(np.fmax(wr, zero) * inv_A)
+    xl = (u + beta * dl) - np.sqrt(np.fmax(wl, zero) * inv_A)
+    return ok, xl, xr
+
+
+def band_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
+    """The binning's ellipse-box test through band_span (see there)."""
+    with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
+        ok, xl, xr = band_span(u, v, A, beta, gamma, qb, Y0, Y1)
+        return ok & (xl <= xr) & (X1 >= xl) & (X0 <= xr)
+
+
 def camera_tensors(cam):
     R = torch.as_tensor(np.asarray(cam.R, np.float64))
     t = torch.as_tensor(np.asarray(cam.t, np.float64))

@@ -26,7 +26,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .project import tile_hit, BIN_MARGIN
+from .project import band_hit, BIN_MARGIN
 
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
@@ -64,7 +64,7 @@ def depth_bits(depth_f32: np.ndarray) -> np.ndarray:
 
 def tile_filter(tile, rec, mean2d, conic_f, q_max, tile_offset, grid_x, widths, heights, tile_w, tile_h):
     """Keep the (tile, record) candidates whose footprint ellipse meets the tile's
-    pixel-centre box; evaluated in the records' dtype (see project.tile_hit)."""
+    pixel-centre box; evaluated in the records' dtype (see project.band_span)."""
     dt = mean2d.dtype.type
     lt = tile - tile_offset[rec]
     gx = grid_x[rec]
@@ -76,7 +76,7 @@ def tile_filter(tile, rec, mean2d, conic_f, q_max, tile_offset, grid_x, widths, 
     Y1 = np.minimum((ty + 1) * tile_h, H).astype(mean2d.dtype) - dt(0.5)
     qb = (q_max.astype(mean2d.dtype) * dt(BIN_MARGIN))[rec]
     cf = conic_f.astype(mean2d.dtype)
-    hit = tile_hit(mean2d[rec, 0], mean2d[rec, 1], cf[rec, 0], cf[rec, 1], cf[rec, 2], qb, X0, X1, Y0, Y1)
+    hit = band_hit(mean2d[rec, 0], mean2d[rec, 1], cf[rec, 0], cf[rec, 1], cf[rec, 2], qb, X0, X1, Y0, Y1)
     return tile[hit], rec[hit]
 
 

@@ -5,7 +5,8 @@
 // alpha can reach the 1/255 floor, with a 0.2% margin) meets the tile's box of pixel
 // centres, ordered by (FP32 depth bits, record index), concatenated tile after tile.
 // Candidate tiles are those under the footprint's bounding box (gs_project's rect);
-// the exact ellipse-box test (tile_hit) removes the rest.
+// per tile row, the ellipse's x-extent over the row's pixel centres keeps a
+// contiguous run of columns (the exact ellipse-box test, band_span_rn).
 //
 // Instead of one wide radix sort on (tile << 32 | depth) keys over all duplicates,
 // the order is built in two stable stages that give the same permutation:
@@ -69,44 +70,41 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(const uint32_t *
 }
 
 // Per-digit exclusive scan of the digit-major histogram hist[256][G] over blocks,
-// in place: one warp per digit (grid of 256 warps), so every row is read and
-// written coalesced and all rows proceed in parallel; the digit total goes to
+// in place: one block of kRsThreads per digit (G <= 4 * kRsThreads), each thread
+// taking up to four consecutive entries of the row; the digit total goes to
 // totals[d]. The digit bases (exclusive scan of totals) are added by the downsweep.
-__global__ void __launch_bounds__(32) rs_scan_kernel(uint32_t *hist, int G, uint32_t *totals,
-                                                      const uint32_t *d_skip) {
+__global__ void __launch_bounds__(kRsThreads) rs_scan_kernel(uint32_t *hist, int G, uint32_t *totals,
+                                                              const uint32_t *d_skip) {
   if (d_skip && *d_skip) return;
-  const int lane = threadIdx.x, d = blockIdx.x;
-  uint32_t *row = hist + (size_t)d * G;
-  uint32_t carry = 0;
-  for (int b0 = 0; b0 < G; b0 += 32) {
-    const int b = b0 + lane;
-    const uint32_t x = b < G ? row[b] : 0u;
-    uint32_t incl = x;
+  uint32_t *row = hist + (size_t)blockIdx.x * G;
+  const int per = (G + kRsThreads - 1) / kRsThreads;
+  const int b0 = threadIdx.x * per;
+  uint32_t x[4] = {0u, 0u, 0u, 0u}, sum = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+  for (int i = 0; i < 4; ++i)
+    if (i < per && b0 + i < G) {
+      x[i] = row[b0 + i];
+      sum += x[i];
     }
-    if (b < G) row[b] = carry + incl - x;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) totals[d] = carry;
+  uint32_t all;
+  uint32_t run = block_exclusive_scan<uint32_t>(sum, &all);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < per && b0 + i < G) {
+      row[b0 + i] = run;
+      run += x[i];
+    }
+  if (threadIdx.x == 0) totals[blockIdx.x] = all;
 }
 
 // Stable scatter. Each warp ranks a contiguous slice of the tile, 32 keys per
-// step in order; slices are then offset by the warps before them, staged in shared
-// memory in digit order and written out coalesced. Ranking within a step: for
-// digits of NB <= 6 bits (BITS = NB), the peers of a key are the AND of NB
-// ballots (one per digit bit) and lane l keeps the running counts of digits l and
-// l + 32 in registers; wider digits (BITS = 0) use __match_any_sync and a per-warp
-// shared-memory count.
-template <int BITS>
+// step in order, with __match_any_sync and a per-warp shared-memory digit count;
+// slices are then offset by the warps before them, staged in shared memory in
+// digit order and written out coalesced.
 __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *d_n, const uint32_t *d_skip, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
-  static_assert(BITS >= 0 && BITS <= 6, "ballot ranking covers digits of at most 6 bits");
-  constexpr int kSlots = BITS == 0 ? 0 : ((1 << BITS) + 31) / 32;
   __shared__ uint32_t s_keys[kRsTile];
   __shared__ uint32_t s_vals[kRsTile];
   __shared__ uint32_t s_whist[kRsWarps][kRsBins + 1];
@@ -124,16 +122,11 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     const uint32_t dbase = block_exclusive_scan<uint32_t>(totals[threadIdx.x], &all);
     s_goff[threadIdx.x] = dbase + hist[(uint64_t)threadIdx.x * G + blockIdx.x];
   }
-  if (BITS > 0) {   // digits >= 2^BITS never occur: zero once
-    for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
-  }
   const uint32_t lt_mask = lanemask_lt();
   for (uint64_t tb = begin; tb < end; tb += kRsTile) {
     const uint32_t tile_n = (uint32_t)min((uint64_t)kRsTile, end - tb);
-    if (BITS == 0) {
-      for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
-      __syncwarp();
-    }
+    for (int d = lane; d < kRsBins + 1; d += 32) s_whist[warp][d] = 0;
+    __syncwarp();
     uint32_t k[kRsItems], v[kRsItems], dig[kRsItems], rank[kRsItems];
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
@@ -143,50 +136,15 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
       v[j] = valid ? vals_in[tb + li] : 0u;
       dig[j] = valid ? ((k[j] >> shift) & mask) : (uint32_t)kRsBins;
     }
-    if (BITS == 0) {
 #pragma unroll
-      for (int j = 0; j < kRsItems; ++j) {
-        const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
-        const uint32_t before = __popc(peers & lt_mask);
-        const uint32_t base = s_whist[warp][dig[j]];
-        __syncwarp();
-        rank[j] = base + before;
-        if (before == 0) s_whist[warp][dig[j]] = base + __popc(peers);
-        __syncwarp();
-      }
-    } else {
-      uint32_t cnt[kSlots > 0 ? kSlots : 1];
-#pragma unroll
-      for (int q = 0; q < kSlots; ++q) cnt[q] = 0;
-#pragma unroll
-      for (int j = 0; j < kRsItems; ++j) {
-        const uint32_t d = dig[j];
-        const uint32_t vm = __ballot_sync(0xffffffffu, d < (uint32_t)kRsBins);
-        uint32_t mb[BITS > 0 ? BITS : 1];
-        uint32_t peers = vm;
-#pragma unroll
-        for (int b = 0; b < BITS; ++b) {
-          mb[b] = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-          peers &= ((d >> b) & 1u) ? mb[b] : ~mb[b];
-        }
-        uint32_t base = __shfl_sync(0xffffffffu, cnt[0], d & 31u);
-        if (kSlots > 1) {
-          const uint32_t hi = __shfl_sync(0xffffffffu, cnt[kSlots > 1 ? 1 : 0], d & 31u);
-          base = ((d >> 5) & 1u) ? hi : base;
-        }
-        rank[j] = base + __popc(peers & lt_mask);
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-          const uint32_t own = lane + 32u * q;   // digit whose count this lane keeps
-          uint32_t m = vm;
-#pragma unroll
-          for (int b = 0; b < BITS; ++b) m &= ((own >> b) & 1u) ? mb[b] : ~mb[b];
-          if (own < (1u << BITS)) cnt[q] += __popc(m);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kSlots; ++q)
-        if (lane + 32 * q < (1 << BITS)) s_whist[warp][lane + 32 * q] = cnt[q];
+    for (int j = 0; j < kRsItems; ++j) {
+      const uint32_t peers = __match_any_sync(0xffffffffu, dig[j]);
+      const uint32_t before = __popc(peers & lt_mask);
+      const uint32_t base = s_whist[warp][dig[j]];
+      __syncwarp();
+      rank[j] = base + before;
+      if (before == 0) s_whist[warp][dig[j]] = base + __popc(peers);
+      __syncwarp();
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -207,7 +165,6 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
-      if (BITS > 0 && dig[j] >= (uint32_t)kRsBins) continue;   // not counted: past the tile's end
       const uint32_t pos = s_tstart[dig[j]] + s_whist[warp][dig[j]] + rank[j];
       s_keys[pos] = k[j];
       s_vals[pos] = v[j];
@@ -270,59 +227,60 @@ struct HistScan {
   }
 };
 
-struct RecordTiles {
-  uint32_t x0, y0, w, n;     // candidate rectangle (origin, width, count)
-  float u, v, A, beta, gamma, qb, ab, inv_den;
+// Per record of a batch (one warp's 32 depth-ordered records), in shared memory:
+// the ellipse constants and the candidate rectangle with its view's layout.
+struct BinRec {
+  float u, v, inv_A, beta, gamma, qb, dyr;
+  uint32_t rec;
+  uint32_t x0, x1, y0;       // candidate tile rectangle (columns [x0, x1), first row y0)
   int W, H, toff, gx;
+  uint32_t pad;
 };
+static_assert(sizeof(BinRec) == 64, "BinRec is four 16-byte words");
 
-__device__ __forceinline__ RecordTiles record_tiles(const gs_proj_t &P, const gs_camera_t *cams, int n_views,
-                                                   int64_t n_per_view, uint32_t r) {
-  RecordTiles t;
-  const uint2 q = reinterpret_cast<const uint2 *>(P.rect)[r];
-  t.x0 = q.x & 0xffffu;
-  t.y0 = q.x >> 16;
-  const uint32_t x1 = q.y & 0xffffu, y1 = q.y >> 16;
-  t.w = x1 > t.x0 ? x1 - t.x0 : 0u;
-  t.n = (x1 > t.x0 && y1 > t.y0) ? t.w * (y1 - t.y0) : 0u;
-  const float2 m = reinterpret_cast<const float2 *>(P.mean2d)[r];
-  const float4 co = reinterpret_cast<const float4 *>(P.conic_opacity)[r];
-  t.u = m.x; t.v = m.y; t.A = co.x; t.beta = co.y; t.gamma = co.z;
-  t.qb = __fmul_rn(reinterpret_cast<const float4 *>(P.rgb)[r].w, kBinMargin);
-  tile_hit_consts(t.A, t.beta, t.gamma, t.ab, t.inv_den);
-  const int view = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
-  t.W = cams[view].width; t.H = cams[view].height; t.toff = cams[view].tile_offset; t.gx = cams[view].grid_x;
-  return t;
+// Columns of one tile row that the band's x-extent [xl, xr] covers: the first tx in
+// [x0, x1) whose pixel-centre box ends at or after xl and the last one that starts
+// at or before xr (exact float compares against the box edges; the scaled
+// coordinate only seeds the search). Returns the count (0 if none) and the first column in lo.
+__device__ __forceinline__ uint32_t band_columns(float xl, float xr, int x0, int x1, int tw, int W, int &lo) {
+  auto X0 = [&](int tx) { return (float)(tx * tw) + 0.5f; };
+  auto X1 = [&](int tx) { return (float)min((tx + 1) * tw, W) - 0.5f; };
+  const float inv_tw = 1.f / (float)tw;
+  int a = (int)fminf(fmaxf(ceilf((xl + 0.5f) * inv_tw) - 1.f, (float)x0), (float)x1);
+  while (a < x1 && X1(a) < xl) ++a;
+  while (a > x0 && X1(a - 1) >= xl) --a;
+  int b = (int)fminf(fmaxf(floorf((xr - 0.5f) * inv_tw), (float)(x0 - 1)), (float)(x1 - 1));
+  while (b >= x0 && X0(b) > xr) --b;
+  while (b + 1 < x1 && X0(b + 1) <= xr) ++b;
+  lo = a;
+  return b >= a ? (uint32_t)(b - a + 1) : 0u;
 }
 
-// Candidate c of the record's rectangle: global tile id and whether the footprint
-// ellipse meets the tile's box of pixel centres.
-__device__ __forceinline__ bool candidate(const RecordTiles &t, uint32_t c, int tw, int th, uint32_t &tile) {
-  const uint32_t tx = t.x0 + c % t.w, ty = t.y0 + c / t.w;
-  tile = (uint32_t)t.toff + ty * (uint32_t)t.gx + tx;
-  const float X0 = (float)(tx * tw) + 0.5f, X1 = (float)min((int)(tx + 1) * tw, t.W) - 0.5f;
-  const float Y0 = (float)(ty * th) + 0.5f, Y1 = (float)min((int)(ty + 1) * th, t.H) - 0.5f;
-  return tile_hit(t.u, t.v, t.A, t.beta, t.gamma, t.ab, t.inv_den, t.qb, X0, X1, Y0, Y1);
-}
-
-// Warp-cooperative pass over the candidate tiles of 32 depth-ordered records at a
-// time (one batch): lane l loads record k0 + l (one round of independent loads),
-// the 32 candidate lists are concatenated by a warp scan, and each lane then takes
-// one candidate per step, finding its record by a binary search over the scan and
-// reading that record's fields with shuffles. Hits are kept in candidate order per
-// digit d = tile & (2^fbits - 1): the count pass (EMIT = false) writes the batch's
-// hits per digit to hist[d * NB + batch]; the emitting pass starts each digit's
-// cursor at the scanned hist entry and writes (tile id, record) at the cursor.
+// Binning of 32 depth-ordered records per warp (one batch), one tile row of a
+// record's candidate rectangle (a "unit") at a time: the ellipse's x-extent over the
+// row's band of pixel centres (band_span_rn) selects a contiguous run of tile
+// columns. Units are spread over the lanes (the batch's rows concatenated by a warp
+// scan, each lane finding its record by a binary search), kUnits per round.
+// COUNT (EMIT = false): every run adds its tiles to the batch's histogram of the
+// low tile digit d = tile & (2^fbits - 1), written to hist[d * NB + batch].
+// EMIT: the round's hits are concatenated again (scan over the units' run lengths)
+// and spread over the lanes; each hit goes to its digit's cursor, which starts at
+// the scanned hist entry and advances in (record, row, column) order, so each
+// digit's entries stay in depth order.
 constexpr int kMaxFusedBits = 8;
+constexpr int kUnits = 64;
 
 template <bool EMIT>
-__global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint32_t *__restrict__ order,
-                                                         const uint32_t *n_vis, const uint32_t *overflow,
-                                                         const gs_camera_t *__restrict__ cams, int n_views,
-                                                         int64_t n_per_view, int tw, int th, int fbits,
-                                                         uint32_t *__restrict__ hist, uint32_t *__restrict__ dkeys,
-                                                         uint32_t *__restrict__ dvals) {
-  __shared__ uint32_t s_cur[8][1 << kMaxFusedBits];   // per warp: hits (count) / next position (emit) per digit
+__global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32_t *__restrict__ order,
+                                                       const uint32_t *n_vis, const uint32_t *overflow,
+                                                       const gs_camera_t *__restrict__ cams, int n_views,
+                                                       int64_t n_per_view, int tw, int th, int fbits,
+                                                       uint32_t *__restrict__ hist, uint32_t *__restrict__ dkeys,
+                                                       uint32_t *__restrict__ dvals) {
+  __shared__ BinRec s_rec[8][32];
+  __shared__ uint2 s_unit[8][kUnits];            // (record slot << 24 | run length, tile id of the run's first column)
+  __shared__ uint32_t s_hpre[8][kUnits + 1];     // exclusive scan of the run lengths
+  __shared__ uint32_t s_cur[8][1 << kMaxFusedBits];
   if (EMIT && *overflow) return;
   const uint32_t nv = *n_vis;
   const uint32_t NB = (nv + 31u) / 32u;
@@ -333,75 +291,134 @@ __global__ void __launch_bounds__(256) candidates_kernel(gs_proj_t P, const uint
   for (uint32_t k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < nv; k0 += nw * 32) {
     const uint32_t batch = k0 / 32u;
     for (uint32_t d = lane; d < nd; d += 32) s_cur[wib][d] = EMIT ? hist[(uint64_t)d * NB + batch] : 0u;
-    const uint32_t k = k0 + lane;
-    RecordTiles t{};
-    uint32_t r = 0;
-    if (k < nv) {
-      r = order[k];
-      t = record_tiles(P, cams, n_views, n_per_view, r);
+    // this lane's record: constants to shared memory, its row count to the scan
+    uint32_t nrow = 0;
+    {
+      const uint32_t k = k0 + lane;
+      BinRec br{};
+      if (k < nv) {
+        const uint32_t r = order[k];
+        const uint2 q = reinterpret_cast<const uint2 *>(P.rect)[r];
+        const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
+        const float2 m = reinterpret_cast<const float2 *>(P.mean2d)[r];
+        const float4 co = reinterpret_cast<const float4 *>(P.conic_opacity)[r];
+        const int view = n_views == 1 ? 0 : (int)((int64_t)r / n_per_view);
+        br.u = m.x; br.v = m.y; br.beta = co.y; br.gamma = co.z;
+        br.qb = __fmul_rn(reinterpret_cast<const float4 *>(P.rgb)[r].w, kBinMargin);
+        band_consts_rn(co.x, br.beta, br.gamma, br.qb, br.dyr, br.inv_A);
+        br.rec = r;
+        br.x0 = x0; br.x1 = x1; br.y0 = y0;
+        br.W = cams[view].width; br.H = cams[view].height; br.toff = cams[view].tile_offset; br.gx = cams[view].grid_x;
+        nrow = (x1 > x0 && y1 > y0) ? y1 - y0 : 0u;
+      }
+      s_rec[wib][lane] = br;
     }
-    uint32_t incl = t.n;
+    uint32_t incl = nrow;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const uint32_t excl = incl - t.n;
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t rexcl = incl - nrow;
+    const uint32_t n_units = __shfl_sync(0xffffffffu, incl, 31);
     __syncwarp();
-    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-      const uint32_t g = c0 + lane;
-      // owner: the last record j whose candidates start at or before g
-      int j = 0;
+    for (uint32_t u0 = 0; u0 < n_units; u0 += kUnits) {
+      uint32_t run[kUnits / 32];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t e = __shfl_sync(0xffffffffu, excl, j + step);
-        if (j + step < 32 && e <= g) j += step;
-      }
-      RecordTiles o;
-      o.x0 = __shfl_sync(0xffffffffu, t.x0, j);
-      o.y0 = __shfl_sync(0xffffffffu, t.y0, j);
-      o.w = __shfl_sync(0xffffffffu, t.w, j);
-      o.n = __shfl_sync(0xffffffffu, t.n, j);
-      o.u = __shfl_sync(0xffffffffu, t.u, j);
-      o.v = __shfl_sync(0xffffffffu, t.v, j);
-      o.A = __shfl_sync(0xffffffffu, t.A, j);
-      o.beta = __shfl_sync(0xffffffffu, t.beta, j);
-      o.gamma = __shfl_sync(0xffffffffu, t.gamma, j);
-      o.qb = __shfl_sync(0xffffffffu, t.qb, j);
-      o.ab = __shfl_sync(0xffffffffu, t.ab, j);
-      o.inv_den = __shfl_sync(0xffffffffu, t.inv_den, j);
-      o.W = __shfl_sync(0xffffffffu, t.W, j);
-      o.H = __shfl_sync(0xffffffffu, t.H, j);
-      o.toff = __shfl_sync(0xffffffffu, t.toff, j);
-      o.gx = __shfl_sync(0xffffffffu, t.gx, j);
-      const uint32_t c = g - __shfl_sync(0xffffffffu, excl, j);
-      uint32_t tile = 0;
-      const bool hit = g < total && candidate(o, c, tw, th, tile);
-      const uint32_t dig = tile & dmask;
-      // hits of this step with the same digit, in lane (= candidate) order
-      const uint32_t peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
-      const uint32_t r_j = EMIT ? __shfl_sync(0xffffffffu, r, j) : 0u;
-      uint32_t cur = 0;
-      if (hit) cur = s_cur[wib][dig];
-      __syncwarp();
-      if (hit) {
-        if (EMIT) {
-          const uint32_t pos = cur + __popc(peers & lt);
-          dkeys[pos] = tile;
-          dvals[pos] = r_j;
+      for (int i = 0; i < kUnits / 32; ++i) {
+        const uint32_t u = u0 + lane + 32 * i;
+        // owner: the last record j whose rows start at or before u
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = __shfl_sync(0xffffffffu, rexcl, j + step);
+          if (j + step < 32 && e <= u) j += step;
         }
-        if ((peers & lt) == 0) s_cur[wib][dig] = cur + __popc(peers);
+        const uint32_t row_j = u - __shfl_sync(0xffffffffu, rexcl, j);
+        run[i] = 0;
+        if (u < n_units) {
+          const BinRec &b = s_rec[wib][j];
+          const int ty = (int)(b.y0 + row_j);
+          const float Y0 = (float)(ty * th) + 0.5f, Y1 = (float)min((ty + 1) * th, b.H) - 0.5f;
+          float xl, xr;
+          int lo = 0;
+          if (band_span_rn(b.u, b.v, b.beta, b.gamma, b.qb, b.dyr, b.inv_A, Y0, Y1, xl, xr))
+            run[i] = band_columns(xl, xr, (int)b.x0, (int)b.x1, tw, b.W, lo);
+          const uint32_t t0 = (uint32_t)(b.toff + ty * b.gx + lo);
+          if (EMIT) {
+            s_unit[wib][u - u0] = make_uint2(((uint32_t)j << 24) | run[i], t0);
+          } else if (run[i] > 0) {
+            // tiles t0 .. t0 + run - 1: digit (t0 + i) & dmask gets ceil((run - i) / nd)
+            const uint32_t nrep = run[i] < nd ? run[i] : nd;
+            for (uint32_t q = 0; q < nrep; ++q)
+              atomicAdd(&s_cur[wib][(t0 + q) & dmask], (run[i] - q + nd - 1) >> fbits);
+          }
+        }
+      }
+      if (EMIT) {
+        // concatenate the round's runs and spread the hits over the lanes
+        uint32_t total = 0;
+#pragma unroll
+        for (int i = 0; i < kUnits / 32; ++i) {
+          uint32_t c = run[i];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += y;
+          }
+          s_hpre[wib][32 * i + lane] = total + c - run[i];
+          total += __shfl_sync(0xffffffffu, c, 31);
+        }
+        if (lane == 0) s_hpre[wib][kUnits] = total;
+        __syncwarp();
+        const uint32_t nu = min((uint32_t)kUnits, n_units - u0);
+        for (uint32_t h0 = 0; h0 < total; h0 += 32) {
+          const uint32_t h = h0 + lane;
+          const bool hit = h < total;
+          uint32_t tile = 0, r = 0;
+          if (hit) {
+            // unit: the last one whose hits start at or before h
+            uint32_t lo = 0, hi = nu;   // invariant: s_hpre[lo] <= h < s_hpre[hi]
+            while (hi - lo > 1) {
+              const uint32_t mid = (lo + hi) >> 1;
+              if (s_hpre[wib][mid] <= h) lo = mid; else hi = mid;
+            }
+            const uint2 un = s_unit[wib][lo];
+            tile = un.y + (h - s_hpre[wib][lo]);
+            r = s_rec[wib][un.x >> 24].rec;
+          }
+          const uint32_t dig = tile & dmask;
+          const uint32_t peers = __match_any_sync(0xffffffffu, hit ? dig : 0xffffffffu);
+          uint32_t cur = 0;
+          if (hit) cur = s_cur[wib][dig];
+          __syncwarp();
+          if (hit) {
+            const uint32_t pos = cur + __popc(peers & lt);
+            dkeys[pos] = tile;
+            dvals[pos] = r;
+            if ((peers & lt) == 0) s_cur[wib][dig] = cur + __popc(peers);
+          }
+          __syncwarp();
+        }
       }
       __syncwarp();
     }
+    __syncwarp();
     if (!EMIT)
       for (uint32_t d = lane; d < nd; d += 32) hist[(uint64_t)d * NB + batch] = s_cur[wib][d];
     __syncwarp();
   }
 }
 
-// ranges[t] = [first index with key >= t, first index with key > t) over the sorted keys.
+// ranges[t] = [first index with key >= t, first index with key > t) over the sorted
+// keys. Each thread takes four consecutive boundaries i = 4g .. 4g+3 (one 16-byte
+// load) and writes the tiles whose range starts or ends there; i = M closes the rest.
+__device__ __forceinline__ void range_boundary(int64_t i, int64_t prev, int64_t cur, int n_tiles,
+                                               uint2 *__restrict__ ranges) {
+  for (int64_t t = prev + 1; t <= cur && t < n_tiles; ++t) ranges[t].x = (uint32_t)i;
+  for (int64_t t = prev < 0 ? 0 : prev; t < cur && t < n_tiles; ++t) ranges[t].y = (uint32_t)i;
+}
+
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *m_total, const uint32_t *overflow,
                               int n_tiles, uint2 *__restrict__ ranges) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -410,12 +427,25 @@ __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t 
     for (int64_t t = tid; t < n_tiles; t += stride) ranges[t] = make_uint2(0u, 0u);
     return;
   }
-  const uint32_t M = *m_total;
-  for (int64_t i = tid; i <= (int64_t)M; i += stride) {
-    const int64_t prev = i > 0 ? (int64_t)keys[i - 1] : -1;
-    const int64_t cur = i < (int64_t)M ? (int64_t)keys[i] : (int64_t)n_tiles;
-    for (int64_t t = prev + 1; t <= cur && t < n_tiles; ++t) ranges[t].x = (uint32_t)i;
-    for (int64_t t = prev < 0 ? 0 : prev; t < cur && t < n_tiles; ++t) ranges[t].y = (uint32_t)i;
+  const int64_t M = *m_total;
+  for (int64_t g = tid; 4 * g <= M; g += stride) {
+    const int64_t i0 = 4 * g;
+    int64_t prev = i0 > 0 ? (int64_t)keys[i0 - 1] : -1;
+    if (i0 + 3 < M) {
+      const uint4 k = *reinterpret_cast<const uint4 *>(keys + i0);
+      const int64_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (kk[j] != prev) range_boundary(i0 + j, prev, kk[j], n_tiles, ranges);
+        prev = kk[j];
+      }
+    } else {
+      for (int64_t i = i0; i <= M && i < i0 + 4; ++i) {
+        const int64_t cur = i < M ? (int64_t)keys[i] : (int64_t)n_tiles;
+        if (cur != prev) range_boundary(i, prev, cur, n_tiles, ranges);
+        prev = cur;
+      }
+    }
   }
 }
 
@@ -489,21 +519,11 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     uint32_t *ki = cur0 ? k0 : k1, *vi = cur0 ? v0 : v1, *ko = cur0 ? k1 : k0, *vo = cur0 ? v1 : v0;
     rs_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, d_n, d_skip, shift, mask, hist);
     GS_LAUNCH_CHECK();
-    rs_scan_kernel<<<kRsBins, 32, 0, s>>>(hist, G, hist + (size_t)kRsBins * kMaxBlocks, d_skip);
+    rs_scan_kernel<<<kRsBins, kRsThreads, 0, s>>>(hist, G, hist + (size_t)kRsBins * kMaxBlocks, d_skip);
     GS_LAUNCH_CHECK();
     const bool last = p == passes - 1;
-    uint32_t *kout = (last && !keep_keys) ? nullptr : ko;
-    const uint32_t *tot = hist + (size_t)kRsBins * kMaxBlocks;
-    switch (nb) {
-#define GS_RS_DOWN(B)                                                                                          \
-  case B:                                                                                                      \
-    rs_downsweep_kernel<B><<<G, kRsThreads, 0, s>>>(ki, vi, kout, vo, d_n, d_skip, shift, mask, hist, tot); \
-    break;
-      GS_RS_DOWN(1) GS_RS_DOWN(2) GS_RS_DOWN(3) GS_RS_DOWN(4) GS_RS_DOWN(5) GS_RS_DOWN(6)
-#undef GS_RS_DOWN
-      default:
-        rs_downsweep_kernel<0><<<G, kRsThreads, 0, s>>>(ki, vi, kout, vo, d_n, d_skip, shift, mask, hist, tot);
-    }
+    rs_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, (last && !keep_keys) ? nullptr : ko, vo, d_n, d_skip,
+                                                 shift, mask, hist, hist + (size_t)kRsBins * kMaxBlocks);
     GS_LAUNCH_CHECK();
     cur0 = !cur0;
   }
@@ -518,8 +538,10 @@ static int bits_for(uint32_t max_value) {
 }
 
 // Tile-id bits and the low digit fused into the emission: every bit above it is
-// covered by ceil((bits - fbits) / 8) radix passes, with fbits as small as that
-// pass count allows (a smaller digit means a smaller (digit, batch) histogram).
+// covered by ceil((bits - 8) / 8) radix passes and fbits takes what they leave.
+// Fewer digits are cheaper to emit: the emission ranks each step's hits by digit
+// and scatters them over 2^fbits output runs (16 digits and one 8-bit pass beat
+// 64 digits and one 6-bit pass on a 4056-tile frame).
 static void tile_sort_plan(int n_tiles, int &tile_bits, int &fbits) {
   tile_bits = bits_for((uint32_t)(n_tiles > 0 ? n_tiles - 1 : 0));
   if (tile_bits <= kMaxFusedBits) {
@@ -572,7 +594,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   //    emission cursors; M and the capacity check
   const int64_t n_per_view = R / frame->n_views;
   const int eg = num_sms() * 8;
-  candidates_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
+  bin_rows_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
                                               n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, nullptr,
                                               nullptr);
   GS_LAUNCH_CHECK();
@@ -583,7 +605,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int passes = (tile_bits - fbits + 7) / 8;
   uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
   const bool emit_to_A = (passes % 2) == 0;
-  candidates_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
+  bin_rows_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist,
                                              emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
   GS_LAUNCH_CHECK();

@@ -85,46 +85,29 @@ __device__ __forceinline__ Falloff falloff(float u, float v, float a2, float bet
   return f;
 }
 
-// Does the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb (d = mean - p) meet the box
-// of pixel centres p in [X0, X1] x [Y0, Y1]? Each operation is one IEEE FP32
-// rounding (no contraction), so the decision is reproducible op for op. If d = 0 is
-// inside the box the test passes; otherwise the minimum of the convex quadratic is
-// on an edge, at the clamped 1-D minimiser.
-__device__ __forceinline__ float qform_rn(float dx, float dy, float A, float beta, float gamma) {
-  const float t = __fadd_rn(dx, __fmul_rn(beta, dy));
-  return __fadd_rn(__fmul_rn(A, __fmul_rn(t, t)), __fmul_rn(gamma, __fmul_rn(dy, dy)));
+// The binning's ellipse-box test, in two steps with one IEEE FP32 rounding per
+// operation (no contraction), so that the decision is reproducible op for op:
+// band_consts_rn once per record, band_span_rn once per row of tiles (the x-extent of
+// the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb, d = mean - p, over the band of
+// pixel-centre rows [Y0, Y1]; derivation beside EllipseRows below), and a box
+// [X0, X1] x [Y0, Y1] meets the ellipse iff ok && xl <= xr && X1 >= xl && X0 <= xr.
+__device__ __forceinline__ void band_consts_rn(float A, float beta, float gamma, float qb, float &dyr,
+                                               float &inv_A) {
+  const float ab = __fmul_rn(A, beta);
+  const float den = __fadd_rn(__fmul_rn(ab, beta), gamma);
+  dyr = __fmul_rn(beta, __fsqrt_rn(__fdiv_rn(__fmul_rn(qb, A), __fmul_rn(gamma, den))));
+  inv_A = __fdiv_rn(1.f, A);
 }
 
-// ab = A beta and inv_den = 1 / (A beta^2 + gamma) are per-record constants
-// (tile_hit_consts); the fixed-dx edge minimiser is dy* = -(A beta dx) / (A beta^2 + gamma).
-__device__ __forceinline__ void tile_hit_consts(float A, float beta, float gamma, float &ab, float &inv_den) {
-  ab = __fmul_rn(A, beta);
-  inv_den = __fdiv_rn(1.f, __fadd_rn(__fmul_rn(ab, beta), gamma));
-}
-
-__device__ __forceinline__ bool tile_hit(float u, float v, float A, float beta, float gamma, float ab, float inv_den,
-                                         float qb, float X0, float X1, float Y0, float Y1) {
-  const float dxl = __fsub_rn(u, X1), dxh = __fsub_rn(u, X0);
+__device__ __forceinline__ bool band_span_rn(float u, float v, float beta, float gamma, float qb, float dyr,
+                                             float inv_A, float Y0, float Y1, float &xl, float &xr) {
   const float dyl = __fsub_rn(v, Y1), dyh = __fsub_rn(v, Y0);
-  if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return true;
-  float m;
-  {
-    const float dx = fminf(fmaxf(-__fmul_rn(beta, dyl), dxl), dxh);
-    m = qform_rn(dx, dyl, A, beta, gamma);
-  }
-  {
-    const float dx = fminf(fmaxf(-__fmul_rn(beta, dyh), dxl), dxh);
-    m = fminf(m, qform_rn(dx, dyh, A, beta, gamma));
-  }
-  {
-    const float dy = fminf(fmaxf(-__fmul_rn(__fmul_rn(ab, dxl), inv_den), dyl), dyh);
-    m = fminf(m, qform_rn(dxl, dy, A, beta, gamma));
-  }
-  {
-    const float dy = fminf(fmaxf(-__fmul_rn(__fmul_rn(ab, dxh), inv_den), dyl), dyh);
-    m = fminf(m, qform_rn(dxh, dy, A, beta, gamma));
-  }
-  return m <= qb;
+  const float dr = fminf(fmaxf(dyr, dyl), dyh), dl = fminf(fmaxf(-dyr, dyl), dyh);
+  const float wr = __fsub_rn(qb, __fmul_rn(gamma, __fmul_rn(dr, dr)));
+  const float wl = __fsub_rn(qb, __fmul_rn(gamma, __fmul_rn(dl, dl)));
+  xr = __fadd_rn(__fadd_rn(u, __fmul_rn(beta, dr)), __fsqrt_rn(__fmul_rn(fmaxf(wr, 0.f), inv_A)));
+  xl = __fsub_rn(__fadd_rn(u, __fmul_rn(beta, dl)), __fsqrt_rn(__fmul_rn(fmaxf(wl, 0.f), inv_A)));
+  return (wr >= 0.f || wl >= 0.f) && xl <= xr;
 }
 
 // x-extent of the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb (d = mean - p) over

@@ -251,6 +251,65 @@ def test_tile_hit_matches_dense_sampling(dtype):
             assert q.min() <= float(qb[i]) * (1 + 1e-5) + grad, i
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_band_hit_matches_dense_sampling(dtype):
+    # the binning's test: a box meets the ellipse iff its column range meets the
+    # ellipse's x-extent over the box's rows; checked against sampled q values
+    rng = np.random.default_rng(13)
+    n = 400
+    cf = _rand_conic_f(rng, n, dtype)
+    u = rng.uniform(-20, 50, n).astype(dtype)
+    v = rng.uniform(-20, 50, n).astype(dtype)
+    qb = rng.uniform(1, 12, n).astype(dtype)
+    X0, X1, Y0, Y1 = (np.full(n, x, dtype) for x in (8.5, 23.5, 16.5, 31.5))
+    hit = oproj.band_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb, X0, X1, Y0, Y1)
+    assert 50 < hit.sum() < n - 50
+    g = np.linspace(0, 1, 61)
+    for i in range(n):
+        PX, PY = np.meshgrid((X0[i] + g * (X1[i] - X0[i])).astype(np.float64),
+                             (Y0[i] + g * (Y1[i] - Y0[i])).astype(np.float64))
+        dx, dy = float(u[i]) - PX, float(v[i]) - PY
+        A, b, c = (float(x) for x in cf[i])
+        q = A * (dx + b * dy) ** 2 + c * dy ** 2
+        if q.min() <= float(qb[i]) * (1 - 1e-5):
+            assert hit[i], i
+        step = np.hypot((X1[i] - X0[i]) / 60, (Y1[i] - Y0[i]) / 60)
+        if hit[i]:
+            grad = 2 * math.sqrt(max(A, c)) * math.sqrt(q.min()) * (1 + abs(b)) * step + 1e-6
+            assert q.min() <= float(qb[i]) * (1 + 1e-5) + grad, i
+
+
+def test_band_hit_equals_box_minimum_test_in_fp64():
+    # two exact formulations of "ellipse meets box" (x-extent over the band vs the
+    # clamped minimum of q on the box): identical except within rounding of qb
+    rng = np.random.default_rng(14)
+    n = 20000
+    cf = _rand_conic_f(rng, n)
+    u = rng.uniform(-25, 55, n)
+    v = rng.uniform(-25, 55, n)
+    qb = rng.uniform(0.5, 12, n)
+    X0, X1, Y0, Y1 = (np.full(n, x) for x in (8.5, 23.5, 16.5, 31.5))
+    a = oproj.band_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb, X0, X1, Y0, Y1)
+    b = oproj.tile_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb, X0, X1, Y0, Y1)
+    near = np.zeros(n, bool)
+    for s in (1 - 1e-9, 1 + 1e-9):
+        near |= oproj.tile_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb * s, X0, X1, Y0, Y1) != b
+    assert 0.15 * n < b.sum() < 0.85 * n
+    assert np.array_equal(a[~near], b[~near])
+
+
+def test_band_span_closed_form_axis_aligned():
+    # beta = 0: the ellipse x^2 A + y^2 gamma <= qb; over a band containing dy = 0 the
+    # extent is u +- sqrt(qb / A); over a band at distance h it is u +- sqrt((qb - gamma h^2) / A)
+    A, g, qb = 0.25, 0.04, 9.0
+    ok, xl, xr = oproj.band_span(np.float64(10.0), np.float64(20.0), A, 0.0, g, qb, 15.5, 25.5)
+    assert ok and xl == 10.0 - 6.0 and xr == 10.0 + 6.0
+    ok, xl, xr = oproj.band_span(np.float64(10.0), np.float64(20.0), A, 0.0, g, qb, 30.0, 40.0)
+    assert ok and math.isclose(xr - 10.0, math.sqrt((qb - g * 100.0) / A)) and math.isclose(xl, 20.0 - xr)
+    ok, _, _ = oproj.band_span(np.float64(10.0), np.float64(20.0), A, 0.0, g, qb, 36.0, 40.0)
+    assert not ok                                    # |dy| > sqrt(qb / gamma) = 15
+
+
 # ------------------------------------------------------------------ binning and sorting
 def _all_pass_records(rect, depth, n):
     """Records whose footprint covers every candidate tile (q_max huge)."""
