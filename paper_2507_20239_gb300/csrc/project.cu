@@ -138,7 +138,9 @@ __device__ __forceinline__ void camera_centre(const gs_camera_t &cam, float &cx,
   cz = -(W[2] * cam.t[0] + W[5] * cam.t[1] + W[8] * cam.t[2]);
 }
 
-template <int DEG>
+// VEC: the SH rows start on 16-byte boundaries (sh_stride a multiple of 4), so a
+// thread reads its row as float4s: 4 coefficients x 3 channels per three loads.
+template <int DEG, bool VEC>
 __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
                                                           int n_views, int tile_w, int tile_h, gs_proj_t out) {
   const int64_t R = (int64_t)n_views * P.n;
@@ -206,11 +208,30 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
     dx *= il; dy *= il; dz *= il;
     const float *sh = P.sh + (int64_t)g * P.sh_stride * 3;
     float cr = 0.5f, cg = 0.5f, cb = 0.5f;
-    sh_visit<DEG>(dx, dy, dz, [&](int k, float Y, float, float, float) {
-      cr = fmaf(Y, sh[3 * k + 0], cr);
-      cg = fmaf(Y, sh[3 * k + 1], cg);
-      cb = fmaf(Y, sh[3 * k + 2], cb);
-    });
+    if (VEC) {
+      constexpr int K = (DEG + 1) * (DEG + 1);
+      float Y[K];
+      sh_visit<DEG>(dx, dy, dz, [&](int k, float y, float, float, float) { Y[k] = y; });
+      const float4 *sh4 = reinterpret_cast<const float4 *>(sh);
+#pragma unroll
+      for (int q = 0; q < (K + 3) / 4; ++q) {
+        const float4 a = sh4[3 * q], b = sh4[3 * q + 1], c = sh4[3 * q + 2];
+        const float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (4 * q + i >= K) break;
+          cr = fmaf(Y[4 * q + i], f[3 * i + 0], cr);
+          cg = fmaf(Y[4 * q + i], f[3 * i + 1], cg);
+          cb = fmaf(Y[4 * q + i], f[3 * i + 2], cb);
+        }
+      }
+    } else {
+      sh_visit<DEG>(dx, dy, dz, [&](int k, float Y, float, float, float) {
+        cr = fmaf(Y, sh[3 * k + 0], cr);
+        cg = fmaf(Y, sh[3 * k + 1], cg);
+        cb = fmaf(Y, sh[3 * k + 2], cb);
+      });
+    }
     const uint8_t cl = (cr < 0.f ? 1 : 0) | (cg < 0.f ? 2 : 0) | (cb < 0.f ? 4 : 0);
     const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
     reinterpret_cast<float2 *>(out.mean2d)[r] = make_float2(u, vv);
@@ -530,12 +551,19 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_frame_t *f
   if (R == 0) return GS_OK;
   const int grid = grid_for(R, 256);
   cudaStream_t s = as_stream(stream);
+  const bool vec = params->sh_stride % 4 == 0 && aligned16(params->sh);
+#define GS_PROJ_FWD(D)                                                                                        \
+  (vec ? project_fwd_kernel<D, true><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views,           \
+                                                          frame->tile_w, frame->tile_h, *out)                \
+       : project_fwd_kernel<D, false><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views,          \
+                                                           frame->tile_w, frame->tile_h, *out))
   switch (params->sh_degree) {
-    case 0: project_fwd_kernel<0><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views, frame->tile_w, frame->tile_h, *out); break;
-    case 1: project_fwd_kernel<1><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views, frame->tile_w, frame->tile_h, *out); break;
-    case 2: project_fwd_kernel<2><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views, frame->tile_w, frame->tile_h, *out); break;
-    default: project_fwd_kernel<3><<<grid, 256, 0, s>>>(*params, frame->cams_dev, frame->n_views, frame->tile_w, frame->tile_h, *out); break;
+    case 0: GS_PROJ_FWD(0); break;
+    case 1: GS_PROJ_FWD(1); break;
+    case 2: GS_PROJ_FWD(2); break;
+    default: GS_PROJ_FWD(3); break;
   }
+#undef GS_PROJ_FWD
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
