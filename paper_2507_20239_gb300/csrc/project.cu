@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(128, 6) project_bwd_geom_kernel(gs_params_t P,
 template <int DEG, bool STAGED, bool ONE_VIEW>
 __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
     gs_params_t P, const gs_camera_t *__restrict__ cams, int n_views, gs_proj_t proj, gs_rec_grads_t rg,
-    gs_param_grads_t out) {
+    gs_param_grads_t out, bool vec) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int RW = 3 * K, RP = RW + 1;
   constexpr bool IN_PLACE = STAGED && ONE_VIEW;
@@ -419,7 +419,15 @@ __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
     const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
     if (STAGED) {
       const float *src = P.sh + g0 * RW;
-      for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
+      if (RW % 4 == 0 && vec) {   // rows of 3K floats, K = 4 or 16: whole float4s, none across rows
+        for (int f4 = lane; f4 < rows * RW / 4; f4 += 32) {
+          const float4 x = reinterpret_cast<const float4 *>(src)[f4];
+          float *d = wsh + ((4 * f4) / RW) * RP + (4 * f4) % RW;
+          d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+        }
+      } else {
+        for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
+      }
       __syncwarp();
     }
     if (g < n) {
@@ -485,7 +493,14 @@ __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
       __syncwarp();
       float *dst = out.d_sh + g0 * RW;
       const float *srow = IN_PLACE ? wsh : s_dsh + wib * 32 * RP;
-      for (int f = lane; f < rows * RW; f += 32) dst[f] = srow[(f / RW) * RP + (f % RW)];
+      if (RW % 4 == 0 && vec) {
+        for (int f4 = lane; f4 < rows * RW / 4; f4 += 32) {
+          const float *q = srow + ((4 * f4) / RW) * RP + (4 * f4) % RW;
+          reinterpret_cast<float4 *>(dst)[f4] = make_float4(q[0], q[1], q[2], q[3]);
+        }
+      } else {
+        for (int f = lane; f < rows * RW; f += 32) dst[f] = srow[(f / RW) * RP + (f % RW)];
+      }
       __syncwarp();
     }
   }
@@ -516,10 +531,13 @@ static void launch_bwd_k(int grid, cudaStream_t s, const gs_params_t &P, const g
                          const gs_rec_grads_t &rg, const gs_param_grads_t &out, float *acc, int32_t *cnt) {
   project_bwd_geom_kernel<<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
   count_launch();
+  // float4 staging needs both SH arrays on 16-byte boundaries (rows of 3K floats, K = 4 or 16)
+  const bool vec = (reinterpret_cast<uintptr_t>(P.sh) & 15u) == 0 && (reinterpret_cast<uintptr_t>(out.d_sh) & 15u) == 0;
   if (frame->n_views == 1)
-    project_bwd_sh_kernel<DEG, STAGED, true><<<grid, 128, 0, s>>>(P, frame->cams_dev, 1, proj, rg, out);
+    project_bwd_sh_kernel<DEG, STAGED, true><<<grid, 128, 0, s>>>(P, frame->cams_dev, 1, proj, rg, out, vec);
   else
-    project_bwd_sh_kernel<DEG, STAGED, false><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out);
+    project_bwd_sh_kernel<DEG, STAGED, false><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out,
+                                                                   vec);
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
