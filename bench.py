@@ -155,6 +155,7 @@ class ViewStep:
         self.bins = R.alloc_bins(frame, Rn, capacity)
         self.image = torch.empty(3 * frame.n_pixels, device=frame.device)
         self.T = torch.empty(frame.n_pixels, device=frame.device)
+        self.stop = torch.empty(frame.n_pixels, dtype=torch.int32, device=frame.device)
         self.d_image = torch.empty_like(self.image)
         self.loss = torch.empty(frame.n_views, device=frame.device)
         self.target = frame.pack_images(sc.targets).contiguous()
@@ -171,11 +172,11 @@ class ViewStep:
         rec(1)
         R.bin_sort_into(self.proj, f, self.bins)
         rec(2)
-        R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T)
+        R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T, store_stop=True, stop=self.stop)
         rec(3)
         R.l1_loss_grad(f, self.image, self.target, d_image=self.d_image, loss=self.loss)
         rec(4)
-        R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec)
+        R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec, stop=self.stop)
         rec(5)
         R.project_bwd(self.P, self.sc.sh_degree, f, self.proj, self.rec, out=self.pgrads,
                       accum=self.stats.accum, count=self.stats.count)

@@ -211,14 +211,16 @@ gs_status_t gs_l1_loss_grad(const gs_frame_t *frame, const float *image, const f
 
 /* Gradient of Eq. 2 w.r.t. every record's mean2d, conic, opacity and colour, given
  * dL/d image. Re-walks each pixel's list front to back with the forward's exact
- * FP32 recurrence (so the stop position is recomputed, not stored) and uses
+ * FP32 recurrence. stop (device, [n_pixels], may be NULL) is the forward's per-pixel
+ * stop index (gs_raster_fwd with store_stop): each pixel then walks only up to it;
+ * with NULL the stop position is recomputed from the transmittance cut-off. Uses
  * dL/dsigma_i = T_i <c_i, g> - (<out, g> - sum_{j<=i} <c_j, g> sigma_j T_j) / (1 - sigma_i),
  * out being the forward's image; zero through the 0.99 clamp. Per-pixel terms are
  * summed per Gaussian in registers, across the warp and the CTA, then added once
  * per (tile, record) into grads (see gs_rec_grads_t). */
 gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                           const gs_raster_cfg_t *cfg, const float *image, const float *d_image,
-                          gs_rec_grads_t *grads, gs_stream_t stream);
+                          const uint32_t *stop, gs_rec_grads_t *grads, gs_stream_t stream);
 
 /* Vector-Jacobian product of gs_project: record gradients -> parameter gradients,
  * summed over views (chain rule through the conic inverse, Sigma' = J W Sigma W^T J^T,

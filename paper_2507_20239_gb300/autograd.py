@@ -32,17 +32,17 @@ class _Rasterize(torch.autograd.Function):
                       opacity_logits=opacity_logits.contiguous(), sh=sh.contiguous())
         proj = R.project(params, sh_degree, frame)
         bins = R.bin_sort(proj, frame)
-        image, T_final, _ = R.raster_fwd(proj, bins, frame, bg)
+        image, T_final, stop = R.raster_fwd(proj, bins, frame, bg, store_stop=True)
         ctx.save_for_backward(*[params[k] for k in R.PARAM_KEYS])
-        ctx.state = (proj, bins, frame, bg, sh_degree, stats, image)
+        ctx.state = (proj, bins, frame, bg, sh_degree, stats, image, stop)
         ctx.mark_non_differentiable(T_final)
         return image, T_final
 
     @staticmethod
     def backward(ctx, d_image, _d_T):
-        proj, bins, frame, bg, sh_degree, stats, image = ctx.state
+        proj, bins, frame, bg, sh_degree, stats, image, stop = ctx.state
         params = dict(zip(R.PARAM_KEYS, ctx.saved_tensors))
-        rec = R.raster_bwd(proj, bins, frame, image, d_image.contiguous(), bg)
+        rec = R.raster_bwd(proj, bins, frame, image, d_image.contiguous(), bg, stop=stop)
         acc = cnt = None
         if stats is not None:
             acc, cnt = stats.accum, stats.count

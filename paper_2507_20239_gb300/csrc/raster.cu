@@ -216,6 +216,7 @@ __device__ __forceinline__ void warp_reduce9_add(const float v[9], float *acc, i
 struct PixBwd {
   float fx, T, S, K, d0, d1, d2;
   bool done;
+  uint32_t stop;   // STOP: one past the pixel's last composited list position
 };
 
 // One pixel's contribution of the current Gaussian. With m = dL/dalpha * G on
@@ -224,14 +225,17 @@ struct PixBwd {
 // gradient (sum d alpha T); the per-record epilogue turns the moments into the
 // gradients w.r.t. (u, v, A, beta, gamma, o) of the quadratic form
 // A (dx + beta dy)^2 + gamma dy^2 with dG/dq = -G/2. co = (k A, beta, k gamma, o).
-__device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, const float4 co,
+// STOP: the forward's stop index bounds the walk (list position jg); before it the
+// transmittance cut-off cannot trigger, so it is not tested.
+template <bool STOP>
+__device__ __forceinline__ bool pix_bwd(PixBwd &p, uint32_t jg, float fy, const float2 xy, const float4 co,
                                         const float4 c, float *v) {
-  if (p.done) return false;
+  if (STOP ? jg >= p.stop : p.done) return false;
   const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, p.fx, fy);
   if (!(f.alpha >= kAlphaMin)) return false;
   const float one_m = __fsub_rn(1.f, f.alpha);
   const float Tn = __fmul_rn(p.T, one_m);
-  if (Tn < kTMin) {
+  if (!STOP && Tn < kTMin) {
     p.done = true;
     return false;
   }
@@ -257,12 +261,15 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, float fy, const float2 xy, co
 // PX pixels per thread: lane l of warp w owns the 2 x (PX/2) block at column
 // 2 (l % 4), row (PX/2) (l / 4) of the warp's 8 x 4PX block, so the per-entry
 // overhead and the warp reduction are shared by PX pixels.
-template <int TW, int TH, int PX>
+// STOP: stop_in holds the forward's per-pixel stop indices; each warp walks up to
+// its pixels' largest, the CTA up to its largest.
+template <int TW, int TH, int PX, bool STOP>
 __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
-    int n_views, const float *__restrict__ image, const float *__restrict__ d_image, float *__restrict__ g_mean2d,
-    float *__restrict__ g_co, float *__restrict__ g_rgb) {
+    int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
+    const uint32_t *__restrict__ stop_in, float *__restrict__ g_mean2d, float *__restrict__ g_co,
+    float *__restrict__ g_rgb) {
   constexpr int NT = TW * TH / PX, BW = 8, BH = 4 * PX;
   __shared__ float2 s_xy[NT];
   __shared__ float4 s_co[NT];
@@ -283,10 +290,11 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
   for (int k = 0; k < PX; ++k) {
     const int px = tc.tx * TW + lx + (k & 1), py = tc.ty * TH + ly + (k >> 1);
     const bool in = py < tc.H && px < tc.W;
-    q[k] = PixBwd{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in};
+    q[k] = PixBwd{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in, 0u};
     if ((k & 1) == 0) fy[k >> 1] = (float)py + 0.5f;
     if (in) {
       const int64_t p = (int64_t)py * tc.W + px;
+      if (STOP) q[k].stop = stop_in[tc.pix_off + p];
       q[k].d0 = dim[p]; q[k].d1 = dim[plane + p]; q[k].d2 = dim[2 * plane + p];
       q[k].K = q[k].d0 * img[p] + q[k].d1 * img[plane + p] + q[k].d2 * img[2 * plane + p];
     }
@@ -298,9 +306,26 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     return d;
   };
   const uint2 rg = ranges[blockIdx.x];
-  const int n = (int)(rg.y - rg.x);
+  int n = (int)(rg.y - rg.x);
+  uint32_t wstop = 0;
+  if (STOP) {
+    __shared__ uint32_t s_cstop;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) m = max(m, q[k].stop);
+    wstop = __reduce_max_sync(0xffffffffu, m);
+    if (t == 0) s_cstop = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(&s_cstop, wstop);
+    __syncthreads();
+    n = min(n, (int)s_cstop);
+  }
   for (int base = 0; base < n; base += NT) {
-    if (__syncthreads_count(!all_done()) == 0) break;
+    if (STOP) {
+      __syncthreads();
+    } else if (__syncthreads_count(!all_done()) == 0) {
+      break;
+    }
     const int cnt = min(NT, n - base);
     if (t < cnt) {
       const uint32_t r = vals[rg.x + base + t];
@@ -311,16 +336,17 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
 #pragma unroll
     for (int k = 0; k < 9; ++k) s_acc[k * NT + t] = 0.f;
     __syncthreads();
-    if (!__all_sync(0xffffffffu, all_done())) {
+    const int jend = STOP ? min(cnt, (int)wstop - base) : cnt;
+    if (STOP ? jend > 0 : !__all_sync(0xffffffffu, all_done())) {
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int j = 0; j < cnt; ++j) {
+      for (int j = 0; j < jend; ++j) {
         const float4 c = s_rgb[j];
         if (!((__float_as_uint(c.w) >> warp) & 1u)) continue;   // warp-uniform skip
         const float2 xy = s_xy[j];
         const float4 co = s_co[j];
         bool any = false;
 #pragma unroll
-        for (int k = 0; k < PX; ++k) any |= pix_bwd(q[k], fy[k >> 1], xy, co, c, v);
+        for (int k = 0; k < PX; ++k) any |= pix_bwd<STOP>(q[k], (uint32_t)(base + j), fy[k >> 1], xy, co, c, v);
         if (__any_sync(0xffffffffu, any)) {
           warp_reduce9_add(v, s_acc + j * 9, lane);
 #pragma unroll
@@ -386,7 +412,8 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
 
 template <int TW, int TH>
 static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
-                              const float *image, const float *d_image, gs_rec_grads_t *g, cudaStream_t s) {
+                              const float *image, const float *d_image, const uint32_t *stop, gs_rec_grads_t *g,
+                              cudaStream_t s) {
   const size_t R = (size_t)proj->n_records;
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
@@ -394,10 +421,18 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
   // 2 pixels per thread: 8 x 8 warp blocks skip more records than 8 x 16 ones
   // (4 pixels per thread) save in shared per-entry work.
   constexpr int PX = 2;
-  raster_bwd_kernel<TW, TH, PX><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
-      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
-      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
-      frame->cams_dev, frame->n_views, image, d_image, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
+  const auto *m2 = reinterpret_cast<const float2 *>(proj->mean2d);
+  const auto *co = reinterpret_cast<const float4 *>(proj->conic_opacity);
+  const auto *c = reinterpret_cast<const float4 *>(proj->rgb);
+  const auto *rg = reinterpret_cast<const uint2 *>(bins->ranges);
+  if (stop)
+    raster_bwd_kernel<TW, TH, PX, true><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
+        m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, stop, g->d_mean2d,
+        g->d_conic_opacity, g->d_rgb);
+  else
+    raster_bwd_kernel<TW, TH, PX, false><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
+        m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, nullptr, g->d_mean2d,
+        g->d_conic_opacity, g->d_rgb);
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
@@ -430,17 +465,17 @@ extern "C" gs_status_t gs_raster_fwd(const gs_proj_t *proj, const gs_bins_t *bin
 
 extern "C" gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                                      const gs_raster_cfg_t *cfg, const float *image, const float *d_image,
-                                     gs_rec_grads_t *grads, gs_stream_t stream) {
+                                     const uint32_t *stop, gs_rec_grads_t *grads, gs_stream_t stream) {
   if (!proj || !bins || !frame || !cfg || !image || !d_image || !grads || !frame->cams_dev || frame->n_tiles <= 0)
     return GS_ERR_INVALID_ARG;
   if (!grads->d_mean2d || !a16(grads->d_conic_opacity) || !a16(grads->d_rgb) || !grads->d_conic_opacity ||
       !grads->d_rgb || ((reinterpret_cast<uintptr_t>(grads->d_mean2d) & 7u) != 0))
     return GS_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
-  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd<16, 16>(proj, bins, frame, image, d_image, grads, s);
-  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, grads, s);
-  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, grads, s);
-  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd<16, 16>(proj, bins, frame, image, d_image, stop, grads, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, stop, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, stop, grads, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, stop, grads, s);
   return GS_ERR_UNSUPPORTED;
 }
 

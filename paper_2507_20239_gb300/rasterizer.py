@@ -281,11 +281,14 @@ class RecGrads:
 
 
 def raster_bwd(proj: Projected, bins: Bins, frame: Frame, image, d_image, bg=(0.0, 0.0, 0.0),
-               grads: Optional[RecGrads] = None, stream=None) -> RecGrads:
+               grads: Optional[RecGrads] = None, stop=None, stream=None) -> RecGrads:
+    """stop: the forward's per-pixel stop indices (raster_fwd(store_stop=True)), or
+    None to recompute them from the transmittance cut-off."""
     grads = RecGrads.zeros(proj.mean2d.shape[0], frame.device) if grads is None else grads
     cfg = raster_cfg(bg)
     check(lib().gs_raster_bwd(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame), C.byref(cfg),
-                              _p(image), _p(_need(d_image, torch.float32, "d_image")), C.byref(grads.struct()),
+                              _p(image), _p(_need(d_image, torch.float32, "d_image")),
+                              _p(stop) if stop is not None else None, C.byref(grads.struct()),
                               _stream(stream)), "gs_raster_bwd")
     return grads
 

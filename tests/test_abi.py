@@ -105,7 +105,7 @@ def test_host_argument_checks_return_invalid_arg(lib):
     assert lib.gs_project(None, C.byref(fr), None, None) == 1
     assert lib.gs_bin_sort(None, None, None, None, 0, None, None) == 1
     assert lib.gs_raster_fwd(None, None, None, None, None, None, None, None) == 1
-    assert lib.gs_raster_bwd(None, None, None, None, None, None, None, None) == 1
+    assert lib.gs_raster_bwd(None, None, None, None, None, None, None, None, None) == 1
     assert lib.gs_project_bwd(None, None, None, None, None, None, None, None) == 1
     assert lib.gs_densify_accum(None, None, None, 0, None, None, None) == 1
     assert lib.gs_l1_loss_grad(None, None, None, None, None, None) == 1

@@ -96,9 +96,12 @@ def test_raster_fwd_ragged_image_and_empty_tiles():
                  frame.view_pixels(stop, 0).cpu().numpy())
 
 
+@pytest.mark.parametrize("use_stop", [False, True])
 @pytest.mark.parametrize("name,tile,bg", [("small", (16, 16), (0, 0, 0)), ("small", (8, 8), (0.2, 0.5, 1.0)),
                                           ("orbit_small", (16, 16), (0.1, 0.2, 0.3))])
-def test_raster_bwd_matches_oracle(name, tile, bg):
+def test_raster_bwd_matches_oracle(name, tile, bg, use_stop):
+    # use_stop: the walk is bounded by the forward's stop indices instead of
+    # re-deriving the cut-off; the gradients are the same
     sc = scene(name)
     cam = sc.cameras[0]
     rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam, tile)
@@ -108,7 +111,7 @@ def test_raster_bwd_matches_oracle(name, tile, bg):
     o, g = _oracle_fwd(rec, cam, tile, bg, d_image=d_image)
     assert o["flag"].sum() <= max(2, 1e-2 * o["flag"].size)
     dg = torch.as_tensor(d_image.reshape(-1)).cuda()
-    rg = R.raster_bwd(proj, bins, frame, img, dg, bg)
+    rg = R.raster_bwd(proj, bins, frame, img, dg, bg, stop=stop if use_stop else None)
     torch.cuda.synchronize()
     got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
                d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
@@ -141,10 +144,11 @@ def test_raster_full_size_sampled_tiles():
     counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
                  frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts, max_flag_frac=5e-2)
-    rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda())
-    torch.cuda.synchronize()
-    got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
-               d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
-    for k in got:
-        e = rel_l2(got[k], g[k])
-        assert e < GRAD_TOL, (k, e)
+    for st in (None, stop):   # recomputed cut-off, and the forward's stop indices (the bench's path)
+        rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda(), stop=st)
+        torch.cuda.synchronize()
+        got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
+                   d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
+        for k in got:
+            e = rel_l2(got[k], g[k])
+            assert e < GRAD_TOL, (k, e, st is not None)
