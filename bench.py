@@ -43,6 +43,8 @@ WORKLOAD = "orbit-1.5M-sh3-1246x826"
 # FLOPs per (pixel, list entry) pair, counted from the oracle's operation list:
 # every examined entry costs the falloff (16); a composited entry adds 10 in the
 # forward (transmittance update, weight, 3 colour FMAs) and 46 in the backward.
+# The forward examines a pixel's entries up to its transmittance cut-off (or the
+# list end); the backward only up to its last composited entry (the stop index).
 FWD_FLOP_EXAM, FWD_FLOP_CONTRIB = 16, 10
 BWD_FLOP_EXAM, BWD_FLOP_CONTRIB = 16, 46
 SM_COUNT_NOMINAL, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
@@ -187,14 +189,36 @@ STAGES = ["project", "bin_sort", "raster_fwd", "l1_loss_grad", "raster_bwd", "pr
 
 
 def measure_capacity(sc, frame, P):
+    """Duplicates M and the per-pixel work of Eq. 2: entries examined by the forward,
+    entries composited, and entries the backward walks (sum of the stop indices)."""
     from paper_2507_20239_gb300 import rasterizer as R
     proj = R.project(P, sc.sh_degree, frame)
     bins = R.bin_sort(proj, frame)
     M = int(bins.count.item())
     counts = R.raster_count(proj, bins, frame)
     c = counts.double().sum(0).cpu().numpy()
+    _, _, stop = R.raster_fwd(proj, bins, frame, store_stop=True)
     measure_capacity.last_counts = counts
-    return M, float(c[0]), float(c[1]), proj
+    return M, float(c[0]), float(c[1]), float(stop.double().sum().item())
+
+
+def capture_step(step, dev):
+    """The step captured once into a CUDA graph (kernel nodes only: every buffer is
+    preallocated), after warm-up on a side stream as graph capture requires."""
+    import torch
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step.run()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step.run()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    return g
 
 
 def bench_ours(args, rank, local_rank, world):
@@ -209,44 +233,51 @@ def bench_ours(args, rank, local_rank, world):
     tile = tuple(int(x) for x in args.tile.split("x"))
     frame = R.Frame(sc.cameras, tile=tile, device=dev)
     P = R.to_device_params(sc.params(), dev)
-    M, p_exam, p_contrib, _ = measure_capacity(sc, frame, P)
+    M, p_exam, p_contrib, p_walk_bwd = measure_capacity(sc, frame, P)
     step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
-    stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         step.run()
     torch.cuda.synchronize()
     assert int(step.bins.error.item()) == 0, "duplicate capacity exceeded"
 
-    # ---- device-resident timed region
+    # ---- per-stage breakdown: the same step launched eagerly, CUDA events between stages
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    launches0 = _abi.load().gs_launch_count()
+    for k in range(args.steps):
+        step.run(events[k])
+    torch.cuda.synchronize()
+    launches = (_abi.load().gs_launch_count() - launches0) // args.steps
+    stage_ms = {s: statistics.mean(events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps))
+                for i, s in enumerate(STAGES)}
+    eager_ms = statistics.mean(events[k][0].elapsed_time(events[k][6]) for k in range(args.steps))
+
+    # ---- device-resident timed region: the step captured once into a CUDA graph
+    graph = capture_step(step, dev)
     clocks = ClockSampler(local_rank)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    launches0 = _abi.load().gs_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
-    for k in range(args.steps):
-        step.run(events[k])
+    for _ in range(args.steps):
+        graph.replay()
     t1.record()
     torch.cuda.synchronize()
-    launches = (_abi.load().gs_launch_count() - launches0) // args.steps
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
-    stage_ms = {s: statistics.mean(events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps))
-                for i, s in enumerate(STAGES)}
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
     if args.quick:
-        print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "stages": stage_ms, "M": M,
+        print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "eager_ms_per_step": round(eager_ms, 4),
+                          "stages": stage_ms, "M": M, "pairs_walked_bwd": p_walk_bwd,
                           "pairs_examined": p_exam, "pairs_composited": p_contrib,
                           "tile_sync": tile_sync_stats(frame, measure_capacity.last_counts)}), flush=True)
         return None
@@ -258,13 +289,13 @@ def bench_ours(args, rank, local_rank, world):
     e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(2):
         step.target.copy_(tgt_host, non_blocking=True)
-        step.run()
+        graph.replay()
     torch.cuda.synchronize()
     e0.record()
     for _ in range(args.steps):
         step.frame.cams_dev.copy_(cam_host, non_blocking=True)
         step.target.copy_(tgt_host, non_blocking=True)
-        step.run()
+        graph.replay()
         loss_host.copy_(step.loss, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
@@ -279,7 +310,7 @@ def bench_ours(args, rank, local_rank, world):
     fp32_peak = SM_COUNT_NOMINAL * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12     # TFLOP/s
     dom = max(stage_ms, key=stage_ms.get)
     flops = {"raster_fwd": FWD_FLOP_EXAM * p_exam + FWD_FLOP_CONTRIB * p_contrib,
-             "raster_bwd": BWD_FLOP_EXAM * p_exam + BWD_FLOP_CONTRIB * p_contrib}
+             "raster_bwd": BWD_FLOP_EXAM * p_walk_bwd + BWD_FLOP_CONTRIB * p_contrib}
     n_rec = sc.n * frame.n_views
     sh_k = sc.sh.shape[1]
     param_bytes = sc.n * 4 * (3 + 3 + 4 + 1 + 3 * sh_k)
@@ -321,12 +352,17 @@ def bench_ours(args, rank, local_rank, world):
         "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_degree": sc.sh_degree,
                    "width": sc.cameras[0].width, "height": sc.cameras[0].height, "tile": args.tile,
                    "views_per_step": frame.n_views, "duplicates_M": M, "pairs_examined": p_exam,
+                   "pairs_walked_bwd": p_walk_bwd,
                    "pairs_composited": p_contrib, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (354 MB parameters read per step)"},
         "e2e": {"value": round(world * 1000.0 / e2e_ms, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(step.target.numel() * 4 + step.frame.cams_dev.numel()),
                 "d2h_bytes_per_step": int(step.loss.numel() * 4)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches) * args.steps,
+        "gpu_launches_per_step": int(launches),
+        "timing": {"value": "CUDA-graph replay of the step, events around the K replays",
+                   "stages": "the same step launched eagerly for K steps just before, events between stages",
+                   "eager_ms_per_step": round(eager_ms, 4)},
         "roofline": roof,
         "stages": stages,
         "clocks": clk,
