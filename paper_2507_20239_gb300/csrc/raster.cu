@@ -81,6 +81,23 @@ __device__ __forceinline__ void stage(const float2 *__restrict__ mean2d, const f
   c.w = __uint_as_float(m);
 }
 
+// The staged positions j < cnt whose block mask has this warp's bit, in order, into
+// list[] (one ballot per 32 entries); returns their number. The walk then visits
+// only those, without a per-entry mask test.
+__device__ __forceinline__ int warp_select(const float4 *s_rgb, int cnt, int warp, int lane, uint8_t *list) {
+  const uint32_t lt = (1u << lane) - 1u;
+  int nsel = 0;
+  for (int j0 = 0; j0 < cnt; j0 += 32) {
+    const int j = j0 + lane;
+    const bool sel = j < cnt && ((__float_as_uint(s_rgb[j].w) >> warp) & 1u);
+    const uint32_t b = __ballot_sync(0xffffffffu, sel);
+    if (sel) list[nsel + __popc(b & lt)] = (uint8_t)j;
+    nsel += __popc(b);
+  }
+  __syncwarp();
+  return nsel;
+}
+
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
@@ -88,11 +105,13 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
     uint32_t *__restrict__ stop_out, uint32_t *__restrict__ counts) {
   constexpr int NT = TW * TH / 2;
+  static_assert(NT <= 256, "list positions are bytes");
   __shared__ float2 s_xy[NT];
   __shared__ float4 s_co[NT];
   __shared__ float4 s_rgb[NT];
+  __shared__ uint8_t s_list[NT / 32][NT];
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   int lx, ly;
   pixel_of<TW>(t, lx, ly);
   const int py = tc.ty * TH + ly;
@@ -116,8 +135,9 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     __syncthreads();
     if (__all_sync(0xffffffffu, done0 && done1)) continue;
     const int cnt = min(NT, n - base);
-    for (int j = 0; j < cnt; ++j) {
-      if (!COUNT && !((__float_as_uint(s_rgb[j].w) >> warp) & 1u)) continue;   // warp-uniform skip
+    const int nsel = COUNT ? cnt : warp_select(s_rgb, cnt, warp, lane, s_list[warp]);
+    for (int i = 0; i < nsel; ++i) {
+      const int j = COUNT ? i : s_list[warp][i];
       const float2 xy = s_xy[j];
       const float4 co = s_co[j];
       if (!done0) {
@@ -277,6 +297,8 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
   __shared__ uint32_t s_rec[NT];
   __shared__ float4 s_cu[NT];
   __shared__ float s_acc[NT * 9];
+  __shared__ uint8_t s_list[NT / 32][NT];
+  static_assert(NT <= 256, "list positions are bytes");
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int lx = (warp % (TW / BW)) * BW + 2 * (lane & 3);
@@ -339,9 +361,10 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     const int jend = STOP ? min(cnt, (int)wstop - base) : cnt;
     if (STOP ? jend > 0 : !__all_sync(0xffffffffu, all_done())) {
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int j = 0; j < jend; ++j) {
+      const int nsel = warp_select(s_rgb, jend, warp, lane, s_list[warp]);
+      for (int i = 0; i < nsel; ++i) {
+        const int j = s_list[warp][i];
         const float4 c = s_rgb[j];
-        if (!((__float_as_uint(c.w) >> warp) & 1u)) continue;   // warp-uniform skip
         const float2 xy = s_xy[j];
         const float4 co = s_co[j];
         bool any = false;
