@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     if (__all_sync(0xffffffffu, done0 && done1)) continue;
     const int cnt = min(NT, n - base);
     const int nsel = COUNT ? cnt : warp_select(s_rgb, cnt, warp, lane, s_list[warp]);
+#pragma unroll 2
     for (int i = 0; i < nsel; ++i) {
       const int j = COUNT ? i : s_list[warp][i];
       const float2 xy = s_xy[j];
