@@ -234,8 +234,10 @@ __device__ __forceinline__ void warp_reduce9_add(const float v[9], float *acc, i
   if (lane == 0) atomicAdd(&acc[8], e);
 }
 
+// R = <out, g> - sum_{j<=i} <c_j, g> sigma_j T_j, the numerator of the second term
+// of dL/dsigma_i, kept as a running remainder.
 struct PixBwd {
-  float fx, T, S, K, d0, d1, d2;
+  float fx, T, R, d0, d1, d2;
   bool done;
   uint32_t stop;   // STOP: one past the pixel's last composited list position
 };
@@ -262,8 +264,8 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, uint32_t jg, float fy, const 
   }
   const float w = f.alpha * p.T;
   const float cd = c.x * p.d0 + c.y * p.d1 + c.z * p.d2;
-  p.S = fmaf(cd, w, p.S);
-  const float dLda = p.T * cd - __fdividef(p.K - p.S, one_m);
+  p.R = fmaf(-cd, w, p.R);
+  const float dLda = p.T * cd - __fdividef(p.R, one_m);
   p.T = Tn;
   v[6] = fmaf(p.d0, w, v[6]);
   v[7] = fmaf(p.d1, w, v[7]);
@@ -313,13 +315,13 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
   for (int k = 0; k < PX; ++k) {
     const int px = tc.tx * TW + lx + (k & 1), py = tc.ty * TH + ly + (k >> 1);
     const bool in = py < tc.H && px < tc.W;
-    q[k] = PixBwd{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, !in, 0u};
+    q[k] = PixBwd{(float)px + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, !in, 0u};
     if ((k & 1) == 0) fy[k >> 1] = (float)py + 0.5f;
     if (in) {
       const int64_t p = (int64_t)py * tc.W + px;
       if (STOP) q[k].stop = stop_in[tc.pix_off + p];
       q[k].d0 = dim[p]; q[k].d1 = dim[plane + p]; q[k].d2 = dim[2 * plane + p];
-      q[k].K = q[k].d0 * img[p] + q[k].d1 * img[plane + p] + q[k].d2 * img[2 * plane + p];
+      q[k].R = q[k].d0 * img[p] + q[k].d1 * img[plane + p] + q[k].d2 * img[2 * plane + p];
     }
   }
   auto all_done = [&]() {
