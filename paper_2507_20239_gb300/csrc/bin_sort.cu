@@ -228,13 +228,15 @@ struct HistScan {
 };
 
 // Per record of a batch (one warp's 32 depth-ordered records), in shared memory:
-// the ellipse constants and the candidate rectangle with its view's layout.
+// the ellipse constants and the candidate rectangle with its view's layout. The
+// counting pass also stores it per depth rank, so that the emitting pass reads it
+// back contiguously instead of gathering the record fields again.
 struct BinRec {
   float u, v, inv_A, beta, gamma, qb, dyr;
   uint32_t rec;
   uint32_t x0, x1, y0;       // candidate tile rectangle (columns [x0, x1), first row y0)
   int W, H, toff, gx;
-  uint32_t pad;
+  uint32_t nrow;             // tile rows of the rectangle (0: nothing to bin)
 };
 static_assert(sizeof(BinRec) == 64, "BinRec is four 16-byte words");
 
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
                                                        const uint32_t *n_vis, const uint32_t *overflow,
                                                        const gs_camera_t *__restrict__ cams, int n_views,
                                                        int64_t n_per_view, int tw, int th, int fbits,
-                                                       uint32_t *__restrict__ hist, uint32_t *__restrict__ dkeys,
-                                                       uint32_t *__restrict__ dvals) {
+                                                       uint32_t *__restrict__ hist, BinRec *__restrict__ brec,
+                                                       uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
   __shared__ BinRec s_rec[8][32];
   __shared__ uint2 s_unit[8][kUnits];            // (record slot << 24 | run length, tile id of the run's first column)
   __shared__ uint32_t s_hpre[8][kUnits + 1];     // exclusive scan of the run lengths
@@ -296,7 +298,12 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
     {
       const uint32_t k = k0 + lane;
       BinRec br{};
-      if (k < nv) {
+      if (EMIT && k < nv) {
+        const float4 *src = reinterpret_cast<const float4 *>(brec + k);
+        float4 *dst = reinterpret_cast<float4 *>(&br);
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+        nrow = br.nrow;
+      } else if (k < nv) {
         const uint32_t r = order[k];
         const uint2 q = reinterpret_cast<const uint2 *>(P.rect)[r];
         const uint32_t x0 = q.x & 0xffffu, y0 = q.x >> 16, x1 = q.y & 0xffffu, y1 = q.y >> 16;
@@ -310,6 +317,10 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
         br.x0 = x0; br.x1 = x1; br.y0 = y0;
         br.W = cams[view].width; br.H = cams[view].height; br.toff = cams[view].tile_offset; br.gx = cams[view].grid_x;
         nrow = (x1 > x0 && y1 > y0) ? y1 - y0 : 0u;
+        br.nrow = nrow;
+        const float4 *src = reinterpret_cast<const float4 *>(&br);
+        float4 *dst = reinterpret_cast<float4 *>(brec + k);
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
       }
       s_rec[wib][lane] = br;
     }
@@ -462,6 +473,7 @@ __global__ void keys64_kernel(const uint32_t *__restrict__ tiles, const uint32_t
 struct BinWs {
   uint32_t *vk0, *vv0, *vk1, *vv1;   // visible records: depth keys / record ids (double buffered)
   uint32_t *dhist;                   // (digit, batch) hit counts -> emission cursors
+  BinRec *brec;                      // per depth rank: binning constants of the record
   uint32_t *dk0, *dk1, *dv1;         // duplicate tile keys (double buffered) + second value buffer
   uint64_t *block_sums;
   uint32_t *hist;
@@ -485,6 +497,7 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap, int fbits) {
   w.vk1 = (uint32_t *)take(4 * (size_t)R + 16);
   w.vv1 = (uint32_t *)take(4 * (size_t)R + 16);
   w.dhist = (uint32_t *)take(4 * ((((size_t)R + 31) / 32) << fbits) + 16);
+  w.brec = (BinRec *)take(sizeof(BinRec) * (size_t)R + 64);
   w.dk0 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dv1 = (uint32_t *)take(4 * (size_t)cap + 16);
@@ -595,8 +608,8 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int64_t n_per_view = R / frame->n_views;
   const int eg = num_sms() * 8;
   bin_rows_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
-                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, nullptr,
-                                              nullptr);
+                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
+                                              nullptr, nullptr);
   GS_LAUNCH_CHECK();
   HistScan hs{w.dhist, n_vis, fbits, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
   if (gs_status_t st = run_scan(hs, w.block_sums, G, s)) return st;
@@ -606,7 +619,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   uint32_t *A_k = w.dk0, *A_v = bins->vals, *B_k = w.dk1, *B_v = w.dv1;
   const bool emit_to_A = (passes % 2) == 0;
   bin_rows_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
-                                             n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist,
+                                             n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
                                              emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
   GS_LAUNCH_CHECK();
   // 5. stable sort by the remaining tile-id bits
