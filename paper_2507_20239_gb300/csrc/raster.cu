@@ -98,6 +98,117 @@ __device__ __forceinline__ int warp_select(const float4 *s_rgb, int cnt, int war
   return nsel;
 }
 
+// Forward without CTA-wide steps: each warp walks its tile's list on its own, 32
+// entries at a time. Lane l gathers entry base + l, tests it against the warp's
+// 8x8 block (the ellipse's x-extent over the block's rows against its columns) and
+// stages it in the warp's shared slots if it passes; the warp then composites the
+// passing entries in list order. A warp leaves as soon as its 64 pixels have
+// stopped, so neither barriers nor finished neighbours hold it.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
+    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
+    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
+    int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
+    uint32_t *__restrict__ stop_out) {
+  constexpr int NW = TW * TH / 64;
+  __shared__ float2 s_xy[NW][32];
+  __shared__ float4 s_co[NW][32];
+  __shared__ float4 s_rgb[NW][32];
+  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  int lx, ly;
+  pixel_of<TW>(t, lx, ly);
+  const int py = tc.ty * TH + ly;
+  const int px = tc.tx * TW + lx;
+  const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
+  const float fy = (float)py + 0.5f, fx0 = (float)px + 0.5f, fx1 = (float)px + 1.5f;
+  // the warp's block of pixel centres
+  const int bx = tc.tx * TW + (warp % (TW / 8)) * 8, by = tc.ty * TH + (warp / (TW / 8)) * 8;
+  const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + 8, tc.W) - 0.5f;
+  const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + 8, tc.H) - 0.5f;
+  float T0 = 1.f, T1 = 1.f;
+  float r0 = 0.f, g0 = 0.f, b0 = 0.f, r1 = 0.f, g1 = 0.f, b1 = 0.f;
+  uint32_t st0 = 0, st1 = 0;
+  bool done0 = !in0, done1 = !in1;
+  const uint2 rg = ranges[blockIdx.x];
+  const int n = (int)(rg.y - rg.x);
+  for (int base = 0; base < n; base += 32) {
+    if (__all_sync(0xffffffffu, done0 && done1)) break;
+    const int j = base + lane;
+    bool sel = false;
+    if (j < n) {
+      const uint32_t r = vals[rg.x + j];
+      const float2 xy = mean2d[r];
+      const float4 co = conic_o[r];
+      const float4 c = rgb[r];
+      const EllipseRows e = ellipse_rows(xy.x, xy.y, co.x, co.y, co.z, c.w * kBinMargin);
+      float xl, xr;
+      sel = row_span(e, Y0, Y1, xl, xr) && X1 >= xl && X0 <= xr;
+      if (sel) {
+        s_xy[warp][lane] = xy;
+        s_co[warp][lane] = make_float4(__fmul_rn(co.x, kNegHalfLog2e), co.y, __fmul_rn(co.z, kNegHalfLog2e), co.w);
+        s_rgb[warp][lane] = c;
+      }
+    }
+    uint32_t b = __ballot_sync(0xffffffffu, sel);
+    __syncwarp();
+    while (b) {
+      const int i = __ffs(b) - 1;
+      b &= b - 1u;
+      const float2 xy = s_xy[warp][i];
+      const float4 co = s_co[warp][i];
+      if (!done0) {
+        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx0, fy);
+        if (f.alpha >= kAlphaMin) {
+          const float Tn = __fmul_rn(T0, __fsub_rn(1.f, f.alpha));
+          if (Tn < kTMin) {
+            done0 = true;
+          } else {
+            const float4 c = s_rgb[warp][i];
+            const float w = f.alpha * T0;
+            r0 = fmaf(c.x, w, r0); g0 = fmaf(c.y, w, g0); b0 = fmaf(c.z, w, b0);
+            T0 = Tn;
+            st0 = base + i + 1;
+          }
+        }
+      }
+      if (!done1) {
+        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx1, fy);
+        if (f.alpha >= kAlphaMin) {
+          const float Tn = __fmul_rn(T1, __fsub_rn(1.f, f.alpha));
+          if (Tn < kTMin) {
+            done1 = true;
+          } else {
+            const float4 c = s_rgb[warp][i];
+            const float w = f.alpha * T1;
+            r1 = fmaf(c.x, w, r1); g1 = fmaf(c.y, w, g1); b1 = fmaf(c.z, w, b1);
+            T1 = Tn;
+            st1 = base + i + 1;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  const int64_t p0 = (int64_t)py * tc.W + px;
+  const int64_t plane = (int64_t)tc.W * tc.H;
+  float *img = image + 3 * tc.pix_off;
+  if (in0) {
+    img[p0] = fmaf(T0, bg0, r0);
+    img[plane + p0] = fmaf(T0, bg1, g0);
+    img[2 * plane + p0] = fmaf(T0, bg2, b0);
+    T_final[tc.pix_off + p0] = T0;
+    if (stop_out) stop_out[tc.pix_off + p0] = st0;
+  }
+  if (in1) {
+    img[p0 + 1] = fmaf(T1, bg0, r1);
+    img[plane + p0 + 1] = fmaf(T1, bg1, g1);
+    img[2 * plane + p0 + 1] = fmaf(T1, bg2, b1);
+    T_final[tc.pix_off + p0 + 1] = T1;
+    if (stop_out) stop_out[tc.pix_off + p0 + 1] = st1;
+  }
+}
+
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
@@ -427,6 +538,15 @@ template <int TW, int TH, bool COUNT = false>
 static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
                               cudaStream_t s, uint32_t *counts = nullptr) {
+  if (!COUNT) {
+    raster_fwd_warp_kernel<TW, TH><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
+        reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
+        reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
+        frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,
+        cfg->store_stop ? stop : nullptr);
+    GS_LAUNCH_CHECK();
+    return GS_OK;
+  }
   raster_fwd_kernel<TW, TH, COUNT><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
