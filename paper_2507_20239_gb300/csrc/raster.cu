@@ -132,15 +132,31 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   bool done0 = !in0, done1 = !in1;
   const uint2 rg = ranges[blockIdx.x];
   const int n = (int)(rg.y - rg.x);
+  // software pipeline: the record id two steps ahead, the record one step ahead
+  uint32_t r_next = lane < n ? vals[rg.x + lane] : 0u;
+  uint32_t r_next2 = 32 + lane < n ? vals[rg.x + 32 + lane] : 0u;
+  float2 xy_n = make_float2(0.f, 0.f);
+  float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f), c_n = co_n;
+  if (lane < n) {
+    xy_n = mean2d[r_next];
+    co_n = conic_o[r_next];
+    c_n = rgb[r_next];
+  }
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
     const int j = base + lane;
+    const float2 xy = xy_n;
+    const float4 co = co_n, c = c_n;
+    // issue the next step's gathers and the id after it before compositing this one
+    r_next = r_next2;
+    if (j + 32 < n) {
+      xy_n = mean2d[r_next];
+      co_n = conic_o[r_next];
+      c_n = rgb[r_next];
+    }
+    r_next2 = j + 64 < n ? vals[rg.x + j + 64] : 0u;
     bool sel = false;
     if (j < n) {
-      const uint32_t r = vals[rg.x + j];
-      const float2 xy = mean2d[r];
-      const float4 co = conic_o[r];
-      const float4 c = rgb[r];
       const EllipseRows e = ellipse_rows(xy.x, xy.y, co.x, co.y, co.z, c.w * kBinMargin);
       float xl, xr;
       sel = row_span(e, Y0, Y1, xl, xr) && X1 >= xl && X0 <= xr;
