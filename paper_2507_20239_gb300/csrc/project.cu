@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
 // Projection VJP, geometric part: conic, pixel mean and opacity gradients of every
 // view -> means (through t = W mu + t_w and J), log-scales, quaternion, opacity
 // logit; the densification statistic is fused. The colour part is project_bwd_sh.
-__global__ void __launch_bounds__(128, 6) project_bwd_geom_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
+__global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
                                                                int n_views, gs_proj_t proj, gs_rec_grads_t rg,
                                                                gs_param_grads_t out, float *accum, int32_t *count) {
   const int64_t n = P.n;
