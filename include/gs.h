@@ -71,6 +71,9 @@ typedef struct {
   int32_t n_tiles;
   int64_t n_pixels;
   int32_t max_width, max_height;
+  int32_t sort_fused_bits; /* gs_bin_sort: low tile-id bits sorted while emitting
+                            * (1..8, at most the tile-id width); 0 = automatic.
+                            * A tuning knob: the order produced is the same. */
 } gs_frame_t;
 
 /* Gaussian parameters, device SoA (Eq. 1: position, scale, rotation, opacity, SH):
@@ -123,6 +126,9 @@ typedef struct {
 typedef struct {
   float bg[3];             /* background colour (default black)                   */
   int32_t store_stop;      /* write the per-pixel stop index in gs_raster_fwd     */
+  int32_t stage_depth;     /* gs_raster_bwd: list entries staged per CTA step,
+                            * 0 = one per thread, 1 = half as many. A tuning
+                            * knob: gradients agree up to summation order. */
 } gs_raster_cfg_t;
 
 /* Gradients of the loss w.r.t. the projected records (device, [R] rows, same row
@@ -163,7 +169,8 @@ gs_status_t gs_frame_init(gs_camera_t *cams_host, int32_t n_views, int32_t tile_
                           int32_t tile_h, gs_frame_t *frame);
 
 /* Bytes of scratch gs_bin_sort needs for n_records records and dup_capacity
- * duplicates on this frame. */
+ * duplicates on this frame (NULL frame: the most any frame needs); 0 for an
+ * invalid size or sort_fused_bits. */
 size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const gs_frame_t *frame);
 
 /* ---------------------------------------------------------------------- hot path */

@@ -20,7 +20,7 @@ class GsCamera(C.Structure):
 class GsFrame(C.Structure):
     _fields_ = [("cams_dev", vp), ("n_views", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("n_tiles", C.c_int32), ("n_pixels", C.c_int64), ("max_width", C.c_int32),
-                ("max_height", C.c_int32)]
+                ("max_height", C.c_int32), ("sort_fused_bits", C.c_int32)]
 
 
 class GsParams(C.Structure):
@@ -38,7 +38,7 @@ class GsBins(C.Structure):
 
 
 class GsRasterCfg(C.Structure):
-    _fields_ = [("bg", C.c_float * 3), ("store_stop", C.c_int32)]
+    _fields_ = [("bg", C.c_float * 3), ("store_stop", C.c_int32), ("stage_depth", C.c_int32)]
 
 
 class GsRecGrads(C.Structure):

@@ -566,6 +566,17 @@ static void tile_sort_plan(int n_tiles, int &tile_bits, int &fbits) {
   if (fbits < 1) fbits = 1;
 }
 
+// The frame's plan: tile_sort_plan, or the frame's sort_fused_bits when set.
+// Returns false for an override outside 1..min(8, tile bits).
+static bool frame_sort_plan(const gs_frame_t *frame, int &tile_bits, int &fbits) {
+  tile_sort_plan(frame->n_tiles, tile_bits, fbits);
+  const int f = frame->sort_fused_bits;
+  if (f == 0) return true;
+  if (f < 1 || f > kMaxFusedBits || f > tile_bits) return false;
+  fbits = f;
+  return true;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -573,7 +584,7 @@ using namespace gs;
 extern "C" size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const gs_frame_t *frame) {
   if (n_records < 0 || dup_capacity < 0) return 0;
   int tile_bits = 32, fbits = kMaxFusedBits;
-  if (frame) tile_sort_plan(frame->n_tiles, tile_bits, fbits);
+  if (frame && !frame_sort_plan(frame, tile_bits, fbits)) return 0;
   return bin_ws_layout(nullptr, n_records, dup_capacity, fbits).bytes;
 }
 
@@ -587,7 +598,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   if (R < 0 || R >= (1ll << 31) || R % frame->n_views != 0) return GS_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return GS_ERR_INVALID_ARG;
   int tile_bits, fbits;
-  tile_sort_plan(frame->n_tiles, tile_bits, fbits);
+  if (!frame_sort_plan(frame, tile_bits, fbits)) return GS_ERR_INVALID_ARG;
   const BinWs w = bin_ws_layout(ws, R, bins->capacity, fbits);
   if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);

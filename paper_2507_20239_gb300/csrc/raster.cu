@@ -412,22 +412,23 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, uint32_t jg, float fy, const 
 // 2 (l % 4), row (PX/2) (l / 4) of the warp's 8 x 4PX block, so the per-entry
 // overhead and the warp reduction are shared by PX pixels.
 // STOP: stop_in holds the forward's per-pixel stop indices; each warp walks up to
-// its pixels' largest, the CTA up to its largest.
-template <int TW, int TH, int PX, bool STOP>
+// its pixels' largest, the CTA up to its largest. HALF: each CTA step stages half
+// as many list entries as the CTA has threads (a finer step, more barriers).
+template <int TW, int TH, int PX, bool STOP, bool HALF>
 __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
     const uint32_t *__restrict__ stop_in, float *__restrict__ g_mean2d, float *__restrict__ g_co,
     float *__restrict__ g_rgb) {
-  constexpr int NT = TW * TH / PX, BW = 8, BH = 4 * PX;
-  __shared__ float2 s_xy[NT];
-  __shared__ float4 s_co[NT];
-  __shared__ float4 s_rgb[NT];
-  __shared__ uint32_t s_rec[NT];
-  __shared__ float4 s_cu[NT];
-  __shared__ float s_acc[NT * 9];
-  __shared__ uint8_t s_list[NT / 32][NT];
+  constexpr int NT = TW * TH / PX, CH = HALF ? NT / 2 : NT, BW = 8, BH = 4 * PX;
+  __shared__ float2 s_xy[CH];
+  __shared__ float4 s_co[CH];
+  __shared__ float4 s_rgb[CH];
+  __shared__ uint32_t s_rec[CH];
+  __shared__ float4 s_cu[CH];
+  __shared__ float s_acc[CH * 9];
+  __shared__ uint8_t s_list[NT / 32][CH];
   static_assert(NT <= 256, "list positions are bytes");
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -472,13 +473,13 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     __syncthreads();
     n = min(n, (int)s_cstop);
   }
-  for (int base = 0; base < n; base += NT) {
+  for (int base = 0; base < n; base += CH) {
     if (STOP) {
       __syncthreads();
     } else if (__syncthreads_count(!all_done()) == 0) {
       break;
     }
-    const int cnt = min(NT, n - base);
+    const int cnt = min(CH, n - base);
     if (t < cnt) {
       const uint32_t r = vals[rg.x + base + t];
       s_rec[t] = r;
@@ -486,7 +487,8 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
                             s_cu[t]);
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s_acc[k * NT + t] = 0.f;
+    for (int k = 0; k < 9; ++k)
+      if (k * NT + t < 9 * CH) s_acc[k * NT + t] = 0.f;
     __syncthreads();
     const int jend = STOP ? min(cnt, (int)wstop - base) : cnt;
     if (STOP ? jend > 0 : !__all_sync(0xffffffffu, all_done())) {
@@ -574,8 +576,8 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
 
 template <int TW, int TH>
 static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
-                              const float *image, const float *d_image, const uint32_t *stop, gs_rec_grads_t *g,
-                              cudaStream_t s) {
+                              const float *image, const float *d_image, const uint32_t *stop, bool half,
+                              gs_rec_grads_t *g, cudaStream_t s) {
   const size_t R = (size_t)proj->n_records;
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
@@ -587,14 +589,15 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
   const auto *co = reinterpret_cast<const float4 *>(proj->conic_opacity);
   const auto *c = reinterpret_cast<const float4 *>(proj->rgb);
   const auto *rg = reinterpret_cast<const uint2 *>(bins->ranges);
+#define GS_BWD(STOPV, HALFV)                                                                               \
+  raster_bwd_kernel<TW, TH, PX, STOPV, HALFV><<<frame->n_tiles, TW * TH / PX, 0, s>>>(                       \
+      m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, stop, g->d_mean2d,          \
+      g->d_conic_opacity, g->d_rgb)
   if (stop)
-    raster_bwd_kernel<TW, TH, PX, true><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
-        m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, stop, g->d_mean2d,
-        g->d_conic_opacity, g->d_rgb);
+    half ? GS_BWD(true, true) : GS_BWD(true, false);
   else
-    raster_bwd_kernel<TW, TH, PX, false><<<frame->n_tiles, TW * TH / PX, 0, s>>>(
-        m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, nullptr, g->d_mean2d,
-        g->d_conic_opacity, g->d_rgb);
+    half ? GS_BWD(false, true) : GS_BWD(false, false);
+#undef GS_BWD
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
@@ -633,11 +636,13 @@ extern "C" gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bin
   if (!grads->d_mean2d || !a16(grads->d_conic_opacity) || !a16(grads->d_rgb) || !grads->d_conic_opacity ||
       !grads->d_rgb || ((reinterpret_cast<uintptr_t>(grads->d_mean2d) & 7u) != 0))
     return GS_ERR_INVALID_ARG;
+  if (cfg->stage_depth != 0 && cfg->stage_depth != 1) return GS_ERR_INVALID_ARG;
+  const bool half = cfg->stage_depth == 1;
   cudaStream_t s = as_stream(stream);
-  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd<16, 16>(proj, bins, frame, image, d_image, stop, grads, s);
-  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, stop, grads, s);
-  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, stop, grads, s);
-  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, stop, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd<16, 16>(proj, bins, frame, image, d_image, stop, half, grads, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, stop, half, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, stop, half, grads, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, stop, half, grads, s);
   return GS_ERR_UNSUPPORTED;
 }
 

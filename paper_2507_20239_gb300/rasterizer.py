@@ -54,7 +54,7 @@ def _bytes(n, device):
 class Frame:
     """A batch of views rendered together (gs_frame_t + a device copy of the cameras)."""
 
-    def __init__(self, cameras, tile=(16, 16), device="cuda"):
+    def __init__(self, cameras, tile=(16, 16), device="cuda", sort_fused_bits=0):
         n = len(cameras)
         arr = (_abi.GsCamera * n)()
         for i, cam in enumerate(cameras):
@@ -70,6 +70,8 @@ class Frame:
             c.near_plane = float(getattr(cam, "near", 0.2))
         self.frame = _abi.GsFrame()
         check(lib().gs_frame_init(arr, n, int(tile[0]), int(tile[1]), C.byref(self.frame)), "gs_frame_init")
+        # low tile-id bits gs_bin_sort sorts while emitting (0 = its own choice)
+        self.frame.sort_fused_bits = int(sort_fused_bits)
         self.cams_host = arr
         raw = bytes(C.string_at(C.addressof(arr), C.sizeof(arr)))
         self.cams_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
@@ -188,7 +190,10 @@ class Bins:
 
 def alloc_bins(frame: Frame, n_records: int, capacity: int, want_keys=False) -> Bins:
     dev = frame.device
-    ws = _bytes(lib().gs_bin_sort_workspace_size(n_records, capacity, C.byref(frame.frame)), dev)
+    ws_size = lib().gs_bin_sort_workspace_size(n_records, capacity, C.byref(frame.frame))
+    if ws_size == 0:
+        raise _abi.GsError(1, "gs_bin_sort_workspace_size (sizes or sort_fused_bits)")
+    ws = _bytes(ws_size, dev)
     return Bins(torch.empty(max(capacity, 1), dtype=torch.int32, device=dev),
                 torch.empty(frame.n_tiles, 2, dtype=torch.int32, device=dev),
                 torch.zeros(1, dtype=torch.int64, device=dev),
@@ -219,11 +224,12 @@ def bin_sort(proj: Projected, frame: Frame, capacity: Optional[int] = None, want
 
 
 # ----------------------------------------------------------------------------------------
-def raster_cfg(bg=(0.0, 0.0, 0.0), store_stop=False) -> _abi.GsRasterCfg:
+def raster_cfg(bg=(0.0, 0.0, 0.0), store_stop=False, stage_depth=0) -> _abi.GsRasterCfg:
     c = _abi.GsRasterCfg()
     for k in range(3):
         c.bg[k] = float(bg[k])
     c.store_stop = 1 if store_stop else 0
+    c.stage_depth = int(stage_depth)
     return c
 
 
@@ -281,11 +287,12 @@ class RecGrads:
 
 
 def raster_bwd(proj: Projected, bins: Bins, frame: Frame, image, d_image, bg=(0.0, 0.0, 0.0),
-               grads: Optional[RecGrads] = None, stop=None, stream=None) -> RecGrads:
+               grads: Optional[RecGrads] = None, stop=None, stage_depth=0, stream=None) -> RecGrads:
     """stop: the forward's per-pixel stop indices (raster_fwd(store_stop=True)), or
-    None to recompute them from the transmittance cut-off."""
+    None to recompute them from the transmittance cut-off. stage_depth: 0 stages one
+    list entry per thread per CTA step, 1 half as many (a tuning knob)."""
     grads = RecGrads.zeros(proj.mean2d.shape[0], frame.device) if grads is None else grads
-    cfg = raster_cfg(bg)
+    cfg = raster_cfg(bg, stage_depth=stage_depth)
     check(lib().gs_raster_bwd(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame), C.byref(cfg),
                               _p(image), _p(_need(d_image, torch.float32, "d_image")),
                               _p(stop) if stop is not None else None, C.byref(grads.struct()),

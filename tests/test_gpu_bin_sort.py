@@ -47,8 +47,8 @@ def _oracle_bins(recs, frame):
     return oras.bin_and_sort(arr, per(3), per(4), per(0), per(1), frame.tile[0], frame.tile[1], frame.n_tiles)
 
 
-def _check(recs, cams, tile, capacity=None):
-    frame = R.Frame(cams, tile=tile)
+def _check(recs, cams, tile, capacity=None, fused_bits=0):
+    frame = R.Frame(cams, tile=tile, sort_fused_bits=fused_bits)
     proj = records_to_gpu(recs)
     keys, vals, ranges = _oracle_bins(recs, frame)
     bins = R.bin_sort(proj, frame, capacity=capacity, want_keys=True)
@@ -72,6 +72,23 @@ def test_bin_sort_mixed_resolution_views():
     cams, _ = synth.mixed_resolution_cameras(6)
     recs = _synthetic_records(10, 30000, cams, (16, 16))
     _check(recs, cams, (16, 16))
+
+
+@pytest.mark.parametrize("fused_bits", [1, 3, 8])
+def test_bin_sort_fused_bits_override(fused_bits):
+    # the number of tile-id bits sorted during emission is a tuning knob: every
+    # choice gives the same keys, order and ranges
+    cams, _ = synth.mixed_resolution_cameras(6)
+    recs = _synthetic_records(11, 20000, cams, (16, 16))
+    _check(recs, cams, (16, 16), fused_bits=fused_bits)
+
+
+def test_bin_sort_rejects_fused_bits_beyond_tile_id_width():
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 50., 50., 17., 9., 35, 19)
+    recs = _synthetic_records(3, 500, [cam], (16, 16))      # 6 tiles: 3-bit tile ids
+    frame = R.Frame([cam], tile=(16, 16), sort_fused_bits=4)
+    with pytest.raises(RuntimeError):
+        R.bin_sort(records_to_gpu(recs), frame)
 
 
 def test_bin_sort_edge_cases():
