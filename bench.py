@@ -12,8 +12,10 @@ in HBM; the 354 MB of parameters the step reads exceed the 129 MB L2.
 Also reported: the same metric end to end (camera and target image copied from
 pinned host memory, loss read back, every step), the roofline of the dominant
 kernel, per-stage times, the batched mixed-resolution form (12 views in one
-launch per stage, CUDA graph) beside its per-view form, and the FP64 oracle timed
-on the host cores on a bounded sample.
+launch per stage, CUDA graph, knobs picked by the autotuner) beside its per-view
+form, the large scene (5M Gaussians, 4 views at 1600x1060) with stored and
+recomputed stop indices and their device memory, and the FP64 oracle timed on the
+host cores on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 (torchrun), every rank renders its own view of its own replica (the
@@ -58,6 +60,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 5M-Gaussian, 4-view section")
     ap.add_argument("--cpu-sample-tiles", type=int, default=160)
     ap.add_argument("--n", type=int, default=1_500_000)
     ap.add_argument("--tile", default="16x16", help="tile shape WxH (16x16, 8x8, 16x32, 32x16)")
@@ -143,48 +146,6 @@ def make_scene(n, rank):
     return sc
 
 
-class ViewStep:
-    """Preallocated buffers and the launch sequence of one fwd+bwd training view."""
-
-    def __init__(self, sc, frame, P, capacity):
-        import torch
-        from paper_2507_20239_gb300 import rasterizer as R
-        from paper_2507_20239_gb300.autograd import DensifyStats
-        self.R = R
-        self.sc, self.frame, self.P = sc, frame, P
-        Rn = frame.n_views * sc.n
-        self.proj = R.Projected.empty(Rn, frame.device)
-        self.bins = R.alloc_bins(frame, Rn, capacity)
-        self.image = torch.empty(3 * frame.n_pixels, device=frame.device)
-        self.T = torch.empty(frame.n_pixels, device=frame.device)
-        self.stop = torch.empty(frame.n_pixels, dtype=torch.int32, device=frame.device)
-        self.d_image = torch.empty_like(self.image)
-        self.loss = torch.empty(frame.n_views, device=frame.device)
-        self.target = frame.pack_images(sc.targets).contiguous()
-        self.rec = R.RecGrads.zeros(Rn, frame.device)
-        self.pgrads = R.empty_param_grads(P)
-        self.stats = DensifyStats.zeros(sc.n, frame.device)
-
-    def run(self, events=None):
-        R, f = self.R, self.frame
-        ev = events or [None] * 7
-        rec = lambda i: ev[i].record() if ev[i] is not None else None
-        rec(0)
-        R.project(self.P, self.sc.sh_degree, f, out=self.proj)
-        rec(1)
-        R.bin_sort_into(self.proj, f, self.bins)
-        rec(2)
-        R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T, store_stop=True, stop=self.stop)
-        rec(3)
-        R.l1_loss_grad(f, self.image, self.target, d_image=self.d_image, loss=self.loss)
-        rec(4)
-        R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec, stop=self.stop)
-        rec(5)
-        R.project_bwd(self.P, self.sc.sh_degree, f, self.proj, self.rec, out=self.pgrads,
-                      accum=self.stats.accum, count=self.stats.count)
-        rec(6)
-
-
 STAGES = ["project", "bin_sort", "raster_fwd", "l1_loss_grad", "raster_bwd", "project_bwd"]
 
 
@@ -202,31 +163,13 @@ def measure_capacity(sc, frame, P):
     return M, float(c[0]), float(c[1]), float(stop.double().sum().item())
 
 
-def capture_step(step, dev):
-    """The step captured once into a CUDA graph (kernel nodes only: every buffer is
-    preallocated), after warm-up on a side stream as graph capture requires."""
-    import torch
-    side = torch.cuda.Stream(device=dev)
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        step.run()
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        step.run()
-    for _ in range(3):
-        g.replay()
-    torch.cuda.synchronize()
-    return g
-
-
 def bench_ours(args, rank, local_rank, world):
     import torch
     import torch.distributed as dist
     from paper_2507_20239_gb300 import build as gbuild
     gbuild.build()
     from paper_2507_20239_gb300 import rasterizer as R, _abi
+    from paper_2507_20239_gb300.step import StepConfig, TrainStep
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     sc = make_scene(args.n, rank)
@@ -234,11 +177,12 @@ def bench_ours(args, rank, local_rank, world):
     frame = R.Frame(sc.cameras, tile=tile, device=dev)
     P = R.to_device_params(sc.params(), dev)
     M, p_exam, p_contrib, p_walk_bwd = measure_capacity(sc, frame, P)
-    step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
+    step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(tile=tile), device=dev,
+                     capacity=int(M * 1.25) + 4096)
     for _ in range(max(args.warmup, 3)):
         step.run()
     torch.cuda.synchronize()
-    assert int(step.bins.error.item()) == 0, "duplicate capacity exceeded"
+    assert step.error() == 0, "duplicate capacity exceeded"
 
     # ---- per-stage breakdown: the same step launched eagerly, CUDA events between stages
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
@@ -252,7 +196,10 @@ def bench_ours(args, rank, local_rank, world):
     eager_ms = statistics.mean(events[k][0].elapsed_time(events[k][6]) for k in range(args.steps))
 
     # ---- device-resident timed region: the step captured once into a CUDA graph
-    graph = capture_step(step, dev)
+    graph = step.capture()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
     if world > 1:
         dist.barrier()
@@ -369,6 +316,8 @@ def bench_ours(args, rank, local_rank, world):
     }
     if rank == 0 and not args.no_batched:
         out["batched"] = bench_batched(args, dev)
+    if rank == 0 and not args.no_large:
+        out["large"] = bench_large(args, dev)
     return out
 
 
@@ -409,25 +358,19 @@ def load_traffic(kernel):
 
 def bench_batched(args, dev):
     """12 mixed-resolution views (4 x 312x207, 4 x 623x413, 4 x 1246x826) of a
-    500k-Gaussian scene: one launch per stage, CUDA-graph captured, against the same
-    kernels launched view by view."""
+    500k-Gaussian scene: the autotuner picks tile shape, fused sort bits and the
+    backward's staging depth; then one launch per stage, CUDA-graph captured, against
+    the same kernels launched view by view."""
     import torch
     from paper_2507_20239_gb300 import rasterizer as R, synth
+    from paper_2507_20239_gb300.autotune import autotune
+    from paper_2507_20239_gb300.step import TrainStep
     sc = synth.batched_scene(2)
     P = R.to_device_params(sc.params(), dev)
-    frame = R.Frame(sc.cameras, device=dev)
-    M, _, _, _ = measure_capacity(sc, frame, P)
-    step = ViewStep(sc, frame, P, int(M * 1.25) + 4096)
-    side = torch.cuda.Stream(device=dev)
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            step.run()
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        step.run()
+    tune = autotune(P, sc.sh_degree, sc.cameras, sc.targets, device=dev)
+    cfg = tune.best
+    step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, cfg, device=dev)
+    g = step.capture(warmup=3)
     for _ in range(3):
         g.replay()
     torch.cuda.synchronize()
@@ -439,35 +382,73 @@ def bench_batched(args, dev):
     e1.record()
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1) / reps
-    # per-view form: the same kernels, one view per launch
-    singles = []
-    for v, cam in enumerate(sc.cameras):
-        f1 = R.Frame([cam], device=dev)
-        sc1 = synth.Scene(sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh, sc.sh_degree, [cam],
-                          [sc.targets[v]])
-        m1, _, _, _ = measure_capacity(sc1, f1, P)
-        singles.append(ViewStep(sc1, f1, P, int(m1 * 1.25) + 4096))
-    for s in singles:
-        s.run()
+    # per-view form: the same kernels and knobs, one view per launch
+    singles = [TrainStep(P, sc.sh_degree, [cam], [sc.targets[v]], cfg, device=dev)
+               for v, cam in enumerate(sc.cameras)]
+    for s1 in singles:
+        s1.run()
     torch.cuda.synchronize()
     e0.record()
     for _ in range(reps):
-        for s in singles:
-            s.run()
+        for s1 in singles:
+            s1.run()
     e1.record()
     torch.cuda.synchronize()
     per_view_ms = e0.elapsed_time(e1) / reps
     # same accuracy: the batched images equal the per-view images
     step.run()
     torch.cuda.synchronize()
-    same = all(torch.equal(frame.view_image(step.image, v), s.frame.view_image(s.image, 0))
-               for v, s in enumerate(singles))
+    same = all(torch.equal(step.frame.view_image(step.image, v), s1.frame.view_image(s1.image, 0))
+               for v, s1 in enumerate(singles))
     nv = len(sc.cameras)
     return {"workload": "batched-500k-sh3-12views-mixed-res", "views_per_launch": nv,
             "batched_views_per_s": round(nv * 1000.0 / batched_ms, 2),
             "per_view_views_per_s": round(nv * 1000.0 / per_view_ms, 2),
             "batched_ms": round(batched_ms, 4), "per_view_ms": round(per_view_ms, 4),
-            "images_identical": bool(same), "graph": True}
+            "images_identical": bool(same), "graph": True, "autotune": tune.as_dict()}
+
+
+def bench_large(args, dev):
+    """5M Gaussians, 4 views at 1600x1060 in one launch per stage (graph-replayed),
+    with the per-pixel stop index stored by the forward and, as where memory binds,
+    recomputed by the backward; device memory beside views/s for both."""
+    import gc
+    import torch
+    from paper_2507_20239_gb300 import rasterizer as R, synth
+    from paper_2507_20239_gb300.step import StepConfig, TrainStep, duplicates
+    sc = synth.large_scene(4)
+    P = R.to_device_params(sc.params(), dev)
+    M = duplicates(P, sc.sh_degree, R.Frame(sc.cameras, device=dev))
+    out = {"workload": "large-5M-sh3-4views-1600x1060", "n_gaussians": sc.n, "views_per_launch": len(sc.cameras),
+           "duplicates_M": M}
+    for mode, store in (("stop_stored", True), ("stop_recomputed", False)):
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        free0, _ = torch.cuda.mem_get_info(dev)
+        base = torch.cuda.memory_allocated(dev)
+        step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(), device=dev,
+                         capacity=int(M * 1.1) + 4096, store_stop=store)
+        g = step.capture(warmup=2)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        assert step.error() == 0, "duplicate capacity exceeded"
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps // 4)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        free1, _ = torch.cuda.mem_get_info(dev)
+        out[mode] = {"views_per_s": round(len(sc.cameras) * 1000.0 / ms, 2), "ms_per_launch": round(ms, 4),
+                     "peak_allocated_gb": round((torch.cuda.max_memory_allocated(dev) - base) / 1e9, 3),
+                     "mem_get_info_delta_gb": round((free0 - free1) / 1e9, 3)}
+        del g, step
+    return out
 
 
 # ----------------------------------------------------------------------------------------
