@@ -1,0 +1,50 @@
+"""The large-scene workload (5M Gaussians, SH degree 3, 4 views at 1600x1060,
+stop indices recomputed by the backward) on sampled outputs: the batched
+projection against the FP64 oracle on 20,000 sampled Gaussians per view, and
+view 0's compositing and gradient on sampled tiles."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_20239_gb300 import rasterizer as R
+from paper_2507_20239_gb300 import synth
+from tests.gs_fixtures import oracle_records_fp32, rel_l2
+from tests.test_gpu_project import _compare_projection
+from tests.test_gpu_raster import GRAD_TOL, _compare_fwd, _gpu, _oracle_fwd, _tile_mask
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def large():
+    return synth.large_scene(4)
+
+
+def test_large_projection_sampled(large):
+    rng = np.random.default_rng(40)
+    sample = np.sort(rng.choice(large.n, 20000, replace=False))
+    _compare_projection(large, large.cameras, sample=sample)
+
+
+def test_large_view_raster_recomputed_stop_sampled_tiles(large):
+    cam = large.cameras[0]
+    tile = (16, 16)
+    rec = oracle_records_fp32(large.params(), large.sh_degree, cam, tile)
+    frame, proj, bins, img, T, stop = _gpu([rec], [cam], tile, (0, 0, 0))
+    ranges = bins.ranges.cpu().numpy()
+    lens = ranges[:, 1] - ranges[:, 0]
+    rng = np.random.default_rng(41)
+    busy = np.nonzero(lens > 0)[0]
+    tiles = sorted(set(rng.choice(busy, 16, replace=False).tolist()) | set(np.argsort(lens)[-2:].tolist()))
+    mask = _tile_mask(cam, tile, tiles)
+    d_image = np.where(mask[None], rng.normal(0, 1, (3, cam.height, cam.width)), 0).astype(np.float32)
+    o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
+    _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, max_flag_frac=5e-2)
+    rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda(), stop=None)
+    torch.cuda.synchronize()
+    got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),
+               d_opacity=rg.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rg.d_rgb[:, :3].cpu().numpy())
+    for k in got:
+        e = rel_l2(got[k], g[k])
+        assert e < GRAD_TOL, (k, e)
