@@ -1,0 +1,204 @@
+"""Training loop of the global-to-local densification schedule (Sec. "Global-to-local
+framework", "Adaptive Opacity Pruning"), on the library's kernels.
+
+Every step renders one view at the current stage's resolution through the
+differentiable rasterizer (autograd.rasterize: gs_project -> gs_bin_sort ->
+gs_raster_fwd, backward gs_raster_bwd -> gs_project_bwd with the densification
+statistic fused), takes the L1 loss gradient with gs_l1_loss_grad and updates the
+parameters with Adam (torch.optim.Adam: the optimiser is plumbing here, not a hot-path
+kernel). Every `densify_every` steps inside [densify_from, densify_until] it runs
+gs_densify_select and gs_densify_apply on the statistics, carrying the Adam moments
+through the compaction (new rows start at zero) and resetting the statistics.
+
+Stages (start step, resolution divisor r, mode): the low-resolution stages run the
+split-only global phase; clone is re-enabled at full resolution. The SH degree in
+use rises by one every `sh_every` steps up to the coefficients stored.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+import torch
+
+from . import rasterizer as R
+from .autograd import DensifyStats, rasterize
+
+PARAM_KEYS = R.PARAM_KEYS
+
+
+@dataclass
+class Schedule:
+    stages: list = field(default_factory=lambda: [(0, 4, R.DENSIFY_SPLIT_ONLY), (1000, 2, R.DENSIFY_SPLIT_ONLY),
+                                                  (2000, 1, R.DENSIFY_ADAPTIVE)])
+    total: int = 3000
+    densify_from: int = 100
+    densify_until: int = 2500
+    densify_every: int = 100
+    sh_every: int = 750
+    grad_threshold: float = 2e-4
+    scale_fraction: float = 0.01       # split when the max scale exceeds this fraction of the extent
+    prune_tau: float = 0.005
+    seed: int = 3
+
+    def stage(self, it):
+        cur = self.stages[0]
+        for s in self.stages:
+            if it >= s[0]:
+                cur = s
+        return cur
+
+    def densify_at(self, it):
+        return self.densify_from <= it <= self.densify_until and it % self.densify_every == 0
+
+
+def default_lrs(extent: float) -> dict:
+    """Learning rates of the 3DGS lineage (one rate for all SH coefficients)."""
+    return {"means": 1.6e-4 * extent, "log_scales": 5e-3, "quats": 1e-3, "opacity_logits": 5e-2, "sh": 2.5e-3}
+
+
+class Trainer:
+    def __init__(self, params: dict, views: dict, schedule: Schedule, extent: float, lrs: Optional[dict] = None,
+                 device="cuda", on_densify: Optional[Callable] = None):
+        """params: numpy float32 arrays (sh [N, K, 3] with K = (d+1)^2 for the final
+        degree d); views: {r: (cameras, target images [3, H, W])} per stage divisor."""
+        self.device = torch.device(device)
+        self.sched, self.extent = schedule, float(extent)
+        self.lrs = lrs or default_lrs(extent)
+        self.max_degree = int(round(math.sqrt(params["sh"].shape[1]))) - 1
+        self.frames = {r: [R.Frame([c], device=device) for c in cams] for r, (cams, _) in views.items()}
+        self.targets = {r: [torch.as_tensor(np.asarray(t, np.float32)).reshape(-1).to(device) for t in tg]
+                        for r, (_, tg) in views.items()}
+        self.on_densify = on_densify
+        self.history = []
+        self.event = 0
+        self._set_params({k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).to(device)
+                          for k, v in params.items()}, None)
+
+    # ---------------------------------------------------------------- state
+    def _set_params(self, tensors: dict, moments: Optional[dict], step=None):
+        self.P = {k: tensors[k].contiguous().requires_grad_(True) for k in PARAM_KEYS}
+        self.opt = torch.optim.Adam([{"params": [self.P[k]], "lr": self.lrs[k], "name": k} for k in PARAM_KEYS],
+                                    eps=1e-15)
+        if moments is not None:
+            for k in PARAM_KEYS:
+                p = self.P[k]
+                self.opt.state[p] = {"step": step.clone() if torch.is_tensor(step) else torch.tensor(float(step)),
+                                     "exp_avg": moments[k + ".m"].reshape(p.shape).contiguous(),
+                                     "exp_avg_sq": moments[k + ".v"].reshape(p.shape).contiguous()}
+        n = self.P["means"].shape[0]
+        self.stats = DensifyStats.zeros(n, self.device)
+
+    @property
+    def n(self):
+        return self.P["means"].shape[0]
+
+    def sh_degree(self, it):
+        return min(self.max_degree, it // self.sched.sh_every)
+
+    # ---------------------------------------------------------------- one step
+    def step(self, it) -> float:
+        _, r, _ = self.sched.stage(it)
+        v = it % len(self.frames[r])
+        frame, target = self.frames[r][v], self.targets[r][v]
+        image, _ = rasterize(self.P, self.sh_degree(it), frame, stats=self.stats)
+        d_image, loss = R.l1_loss_grad(frame, image.detach(), target)
+        image.backward(d_image)
+        self.opt.step()
+        self.opt.zero_grad(set_to_none=True)
+        return loss
+
+    # ---------------------------------------------------------------- densification
+    def densify(self, it):
+        _, r, mode = self.sched.stage(it)
+        thr_s = np.float32(math.log(self.sched.scale_fraction * self.extent))
+        prune_logit = np.float32(math.log(self.sched.prune_tau / (1.0 - self.sched.prune_tau)))
+        cfg = R.densify_cfg(mode=mode, grad_threshold=self.sched.grad_threshold, log_scale_threshold=thr_s,
+                            prune_logit=prune_logit, seed=self.sched.seed, event=self.event)
+        P = {k: self.P[k].detach() for k in PARAM_KEYS}
+        split, clone, tau, new_n, ws = R.densify_select(cfg, P, self.stats.accum, self.stats.count)
+        extra, step = {}, None
+        for k in PARAM_KEYS:
+            st = self.opt.state.get(self.P[k], {})
+            if "exp_avg" in st:
+                extra[k + ".m"] = st["exp_avg"].reshape(self.n, -1).contiguous()
+                extra[k + ".v"] = st["exp_avg_sq"].reshape(self.n, -1).contiguous()
+                step = st["step"]
+        cap = int(new_n.item())
+        out, ex, got_n, err = R.densify_apply(cfg, P, self.sh_degree(it), split, clone, tau, cap, extra=extra,
+                                              ws=ws)
+        if int(err.item()) != 0 or int(got_n.item()) != cap:
+            raise RuntimeError("densify: output capacity")
+        if self.on_densify is not None:
+            self.on_densify(dict(it=it, mode=mode, cfg=cfg, thr_s=thr_s, prune_logit=prune_logit,
+                                 params=P, accum=self.stats.accum, count=self.stats.count, extra=extra,
+                                 split=split, clone=clone, tau=tau, out=out, out_extra=ex, seed=self.sched.seed,
+                                 event=self.event))
+        self.event += 1
+        self._set_params(out, ex if extra else None, step)
+
+    def run(self, log_every: int = 100):
+        for it in range(1, self.sched.total + 1):
+            loss = self.step(it - 1)
+            if self.sched.densify_at(it):
+                self.densify(it)
+            if it % log_every == 0 or it == self.sched.total:
+                self.history.append((it, self.n, float(loss[0].item())))
+        return self.history
+
+
+def render_targets(gt_params: dict, sh_degree: int, cameras, device="cuda") -> list:
+    """Target images of a ground-truth scene rendered by the library's forward."""
+    P = R.to_device_params(gt_params, device)
+    out = []
+    for cam in cameras:
+        frame = R.Frame([cam], device=device)
+        proj = R.project(P, sh_degree, frame)
+        bins = R.bin_sort(proj, frame)
+        img, _, _ = R.raster_fwd(proj, bins, frame)
+        out.append(frame.view_image(img, 0).cpu().numpy())
+    return out
+
+
+def orbit_views(n_views: int, width: int, height: int, f: float, divisors=(4, 2, 1), radius=4.0, elevation=15.0):
+    """n_views orbit cameras per resolution divisor r (W/r rounded half up)."""
+    from . import synth
+    out = {}
+    for r in divisors:
+        w, h = int(math.floor(width / r + 0.5)), int(math.floor(height / r + 0.5))
+        out[r] = [synth.orbit_camera(radius, 2 * math.pi * k / n_views, elevation, w, h, f / r) for k in range(n_views)]
+    return out
+
+
+def main(argv=None):
+    """The densification trajectory of the training-loop workload: targets rendered
+    from a 1.5M-Gaussian scene (seed 13) at 8 orbit views per resolution, training
+    from 100k Gaussians (seed 3) for 3,000 steps; prints the (step, N, loss) history."""
+    import argparse
+    import json
+    from . import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gt", type=int, default=1_500_000)
+    ap.add_argument("--init", type=int, default=100_000)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--width", type=int, default=1246)
+    ap.add_argument("--height", type=int, default=826)
+    ap.add_argument("--views", type=int, default=8)
+    args = ap.parse_args(argv)
+    s = args.steps / 3000.0
+    sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
+                             (int(2000 * s), 1, R.DENSIFY_ADAPTIVE)], total=args.steps,
+                     densify_until=int(2500 * s), sh_every=max(1, int(750 * s)))
+    cams = orbit_views(args.views, args.width, args.height, float(args.width))
+    gt = synth.surface_scene(13, args.gt, 3)
+    views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
+    init = synth.surface_scene(3, args.init, 3).params()
+    tr = Trainer(init, views, sched, extent=1.1 * 4.0)
+    hist = tr.run()
+    print(json.dumps({"history": hist, "final_n": tr.n}))
+
+
+if __name__ == "__main__":
+    main()

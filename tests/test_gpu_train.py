@@ -1,0 +1,60 @@
+"""The training-loop workload, shortened: the global-to-local schedule (split-only
+at 1/4 and 1/2 resolution, clone re-enabled at full resolution, prune below
+opacity 0.005, SH degree rising) trained on the library's kernels, with every
+densification event checked against the oracle on the same FP32 tensors: split and
+clone masks, the prune threshold and the whole compaction (parameters and the Adam
+moments carried through it) bit-exact, split children's means within 1e-5."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import densify as oden
+from paper_2507_20239_gb300 import rasterizer as R
+from paper_2507_20239_gb300 import synth
+from paper_2507_20239_gb300.train import Schedule, Trainer, orbit_views, render_targets
+
+pytestmark = pytest.mark.gpu
+
+
+def test_global_to_local_training_with_checked_densification():
+    events = []
+
+    def check(ev):
+        np_ = lambda t: t.detach().cpu().numpy()
+        p = {k: np_(v) for k, v in ev["params"].items()}
+        accum, count = np_(ev["accum"]), np_(ev["count"])
+        ws_, wc = oden.select(accum, count, p["log_scales"], ev["mode"], np.float32(2e-4), ev["thr_s"])
+        assert np.array_equal(np_(ev["split"]).astype(bool), ws_)
+        assert np.array_equal(np_(ev["clone"]).astype(bool), wc)
+        tau = oden.prune_threshold(p["opacity_logits"], ws_, wc, fixed_tau=0.005)
+        assert np.float32(ev["tau"].item()) == tau
+        extra = {k: np_(v) for k, v in ev["extra"].items()}
+        want, wex, idx = oden.apply(p, ws_, wc, tau, ev["seed"], ev["event"], extra=extra)
+        out = {k: np_(v) for k, v in ev["out"].items()}
+        assert out["means"].shape[0] == len(idx["source"])
+        for k in ("log_scales", "quats", "opacity_logits", "sh"):
+            assert np.array_equal(out[k], want[k]), k
+        for k in extra:
+            assert np.array_equal(np_(ev["out_extra"][k]), wex[k]), k
+        base = out["means"].shape[0] - 2 * len(idx["splits"])
+        assert np.array_equal(out["means"][:base], want["means"][:base].astype(np.float32))
+        if base < out["means"].shape[0]:
+            assert np.abs(out["means"][base:] - want["means"][base:]).max() < 1e-5
+        events.append((ev["it"], ev["mode"], int(ws_.sum()), int(wc.sum()), len(idx["source"])))
+
+    cams = orbit_views(4, 623, 413, 623.0)
+    gt = synth.surface_scene(13, 200_000, 3)
+    views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
+    init = synth.surface_scene(3, 20_000, 3).params()
+    sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (200, 2, R.DENSIFY_SPLIT_ONLY),
+                             (400, 1, R.DENSIFY_ADAPTIVE)], total=600, densify_until=500, sh_every=150)
+    tr = Trainer(init, views, sched, extent=1.1 * 4.0, on_densify=check)
+    hist = tr.run(log_every=50)
+    assert [e[0] for e in events] == [100, 200, 300, 400, 500]
+    assert all(e[1] == R.DENSIFY_SPLIT_ONLY for e in events[:3]) and events[3][1] == R.DENSIFY_ADAPTIVE
+    assert all(e[3] == 0 for e in events[:3])                     # no clones in the split-only phase
+    assert sum(e[2] for e in events) > 0 and sum(e[3] for e in events[3:]) > 0
+    assert tr.n > 20_000
+    assert hist[-1][2] < hist[0][2]                                # the L1 loss went down
