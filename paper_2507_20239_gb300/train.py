@@ -186,18 +186,23 @@ def main(argv=None):
     ap.add_argument("--width", type=int, default=1246)
     ap.add_argument("--height", type=int, default=826)
     ap.add_argument("--views", type=int, default=8)
+    ap.add_argument("--init-log-scale", type=float, default=-4.0,
+                    help="mean log-scale of the initial Gaussians (the generator's default: -4)")
+    ap.add_argument("--grad-threshold", type=float, default=2e-4)
     args = ap.parse_args(argv)
     s = args.steps / 3000.0
     sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
                              (int(2000 * s), 1, R.DENSIFY_ADAPTIVE)], total=args.steps,
-                     densify_until=int(2500 * s), sh_every=max(1, int(750 * s)))
+                     densify_until=int(2500 * s), sh_every=max(1, int(750 * s)),
+                     grad_threshold=args.grad_threshold)
     cams = orbit_views(args.views, args.width, args.height, float(args.width))
     gt = synth.surface_scene(13, args.gt, 3)
     views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
-    init = synth.surface_scene(3, args.init, 3).params()
+    init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
     tr = Trainer(init, views, sched, extent=1.1 * 4.0)
     hist = tr.run()
-    print(json.dumps({"history": hist, "final_n": tr.n}))
+    print(json.dumps({"history": hist, "final_n": tr.n, "init_log_scale": args.init_log_scale,
+                      "grad_threshold": args.grad_threshold}))
 
 
 if __name__ == "__main__":
