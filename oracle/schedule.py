@@ -46,7 +46,7 @@ def downscale(img: np.ndarray, r: int) -> np.ndarray:
         return img.copy()
     Wy = aa_weights(H, downscaled_size(H, r))
     Wx = aa_weights(W, downscaled_size(W, r))
-    return np.einsum("yh,chw,xw->cyx", Wy, img, Wx)
+    return np.stack([Wy @ c @ Wx.T for c in img])
 
 
 def spectrum_l1(img: np.ndarray) -> float:
