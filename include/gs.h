@@ -335,6 +335,32 @@ gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in,
                              int64_t out_capacity, int64_t *d_new_n, int32_t *d_error,
                              void *ws, size_t ws_bytes, gs_stream_t stream);
 
+/* ------------------------------------------------- coarse-to-fine schedule energy */
+/* Sec. "Energy-aware multi-resolution": the downscaling operator D_r (bilinear with
+ * anti-aliasing) and the energy ||E(I)||_1 = sum over channels and frequencies of
+ * the magnitude of the 2D DFT. The schedule built on them (E_r = ||E(D_r(I))||_1 r^2,
+ * T_r = Round(E_r / E_1 T_densify)) is host arithmetic in the Python binding. */
+
+/* Rows or columns after D_r: floor(n / r + 1/2), at least 1 (0 for bad input). */
+int32_t gs_downscaled_size(int32_t n, int32_t r);
+
+/* D_r of a planar image [C][H][W] (device, FP32) into out [C][Hr][Wr] (device,
+ * Hr x Wr = gs_downscaled_size of H x W): separable triangle filter of half-width
+ * s = W / Wr (rows: H / Hr); output column j samples the input at (j + 1/2) s - 1/2,
+ * weights max(0, 1 - |k - c| / s) over the columns inside the image, normalised to
+ * sum 1. r = 1 copies. */
+gs_status_t gs_downscale(const float *image, int32_t C, int32_t H, int32_t W, int32_t r, float *out,
+                         gs_stream_t stream);
+
+/* Bytes of scratch gs_spectrum_l1 needs (0 if C < 1 or H, W outside 1..4096). */
+size_t gs_spectrum_workspace_size(int32_t C, int32_t H, int32_t W);
+
+/* ||E(I)||_1 of a planar image [C][H][W] (device, FP32), written to *d_sum (device,
+ * one double, overwritten). Unnormalised forward DFT, FP32 products, FP64 sums of the
+ * magnitudes. ws: 16-byte aligned, gs_spectrum_workspace_size bytes. */
+gs_status_t gs_spectrum_l1(const float *image, int32_t C, int32_t H, int32_t W, double *d_sum, void *ws,
+                           size_t ws_bytes, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,10 @@ SIGNATURES = {
     "gs_densify_select_static": (C.c_int, [P(GsDensifyCfg), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
     "gs_densify_apply": (C.c_int, [P(GsDensifyCfg), P(GsParams), vp, vp, vp, P(GsParamsOut),
                                    P(GsExtraArray), C.c_int32, C.c_int64, vp, vp, vp, C.c_size_t, vp]),
+    "gs_downscaled_size": (C.c_int32, [C.c_int32, C.c_int32]),
+    "gs_downscale": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]),
+    "gs_spectrum_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "gs_spectrum_l1": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_size_t, vp]),
 }
 
 _lib = None
