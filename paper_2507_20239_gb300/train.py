@@ -149,6 +149,35 @@ class Trainer:
         return self.history
 
 
+def scaled_camera(cam, width: int, height: int):
+    """The camera whose pixel grid is D_r's output grid: intrinsics scaled by the
+    actual size ratios (output pixel j covers input [j s, (j + 1) s))."""
+    from . import synth
+    sx, sy = width / cam.width, height / cam.height
+    return synth.Camera(cam.R, cam.t, cam.fx * sx, cam.fy * sy, cam.cx * sx, cam.cy * sy, width, height)
+
+
+def energy_stages(cameras, full_targets, K: int, T_densify: int, device="cuda"):
+    """Stages and per-scale views from the energy schedule of the full-resolution
+    targets: scale r > 1 runs the split-only phase on D_r(targets), r = 1 the
+    adaptive phase. Returns (stages [(start, r, mode)], views {r: (cams, targets)},
+    (E, T))."""
+    from . import schedule as S
+    E, T, st = S.energy_schedule(full_targets, K=K, T_densify=T_densify, device=device)
+    stages = [(start, r, R.DENSIFY_SPLIT_ONLY if r > 1 else R.DENSIFY_ADAPTIVE) for start, _, r in st]
+    if not stages or stages[-1][1] != 1:
+        stages.append((T_densify, 1, R.DENSIFY_ADAPTIVE))
+    views = {}
+    for _, r, _ in stages:
+        if r in views:
+            continue
+        imgs = [torch.as_tensor(np.asarray(t, np.float32)).to(device) for t in full_targets]
+        small = [S.downscale(t, r).cpu().numpy() if r > 1 else t.cpu().numpy() for t in imgs]
+        cams = [scaled_camera(c, im.shape[2], im.shape[1]) for c, im in zip(cameras, small)]
+        views[r] = (cams, small)
+    return stages, views, (E, T)
+
+
 def render_targets(gt_params: dict, sh_degree: int, cameras, device="cuda") -> list:
     """Target images of a ground-truth scene rendered by the library's forward."""
     P = R.to_device_params(gt_params, device)
@@ -189,20 +218,31 @@ def main(argv=None):
     ap.add_argument("--init-log-scale", type=float, default=-4.0,
                     help="mean log-scale of the initial Gaussians (the generator's default: -4)")
     ap.add_argument("--grad-threshold", type=float, default=2e-4)
+    ap.add_argument("--energy", type=int, default=0, metavar="K",
+                    help="derive the stages from the targets' energy schedule with scales 1..K "
+                         "(default: fixed thirds at 1/4, 1/2, full resolution)")
     args = ap.parse_args(argv)
     s = args.steps / 3000.0
     sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
                              (int(2000 * s), 1, R.DENSIFY_ADAPTIVE)], total=args.steps,
                      densify_until=int(2500 * s), sh_every=max(1, int(750 * s)),
                      grad_threshold=args.grad_threshold)
-    cams = orbit_views(args.views, args.width, args.height, float(args.width))
     gt = synth.surface_scene(13, args.gt, 3)
-    views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
+    energy = None
+    if args.energy:
+        full = orbit_views(args.views, args.width, args.height, float(args.width), divisors=(1,))[1]
+        targets = render_targets(gt.params(), 3, full)
+        stages, views, (E, T) = energy_stages(full, targets, args.energy, sched.densify_until)
+        sched.stages = stages
+        energy = {"E": [float(e) for e in E], "T": [int(t) for t in T], "stages": stages}
+    else:
+        cams = orbit_views(args.views, args.width, args.height, float(args.width))
+        views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
     init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
     tr = Trainer(init, views, sched, extent=1.1 * 4.0)
     hist = tr.run()
     print(json.dumps({"history": hist, "final_n": tr.n, "init_log_scale": args.init_log_scale,
-                      "grad_threshold": args.grad_threshold}))
+                      "grad_threshold": args.grad_threshold, "energy_schedule": energy}))
 
 
 if __name__ == "__main__":

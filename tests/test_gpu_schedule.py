@@ -53,3 +53,22 @@ def test_spectrum_rejects_oversized_images():
     assert S.lib().gs_spectrum_workspace_size(3, 4097, 100) == 0
     with pytest.raises(RuntimeError):
         S.spectrum_l1(torch.zeros(1, 4097, 8, device="cuda"))
+
+
+def test_energy_schedule_drives_training():
+    from paper_2507_20239_gb300 import rasterizer as R, synth
+    from paper_2507_20239_gb300.train import Schedule, Trainer, energy_stages, orbit_views, render_targets
+    full = orbit_views(2, 320, 212, 320.0, divisors=(1,))[1]
+    gt = synth.surface_scene(13, 60_000, 3)
+    targets = render_targets(gt.params(), 3, full)
+    stages, views, (E, T) = energy_stages(full, targets, 4, 300)
+    assert stages[0][0] == 0 and stages[-1][1] == 1
+    assert [s[1] for s in stages] == sorted((s[1] for s in stages), reverse=True)      # coarse to fine
+    assert all(m == R.DENSIFY_SPLIT_ONLY for _, r, m in stages if r > 1)
+    for r, (cams, imgs) in views.items():
+        assert imgs[0].shape == (3, S.downscaled_size(212, r), S.downscaled_size(320, r))
+        assert cams[0].width == imgs[0].shape[2]
+    sched = Schedule(stages=stages, total=400, densify_until=300, sh_every=100)
+    tr = Trainer(synth.surface_scene(3, 10_000, 3).params(), views, sched, extent=4.4)
+    hist = tr.run(log_every=100)
+    assert tr.event == 3 and hist[-1][2] < hist[0][2]
