@@ -335,6 +335,47 @@ gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in,
                              int64_t out_capacity, int64_t *d_new_n, int32_t *d_error,
                              void *ws, size_t ws_bytes, gs_stream_t stream);
 
+/* ------------------------------------------------------------ training step */
+/* Eq. 3: L = (1 - lambda) ||I - I_hat||_1 + lambda D-SSIM(I, I_hat), per view: the L1
+ * term as the mean over 3 H W values, D-SSIM = 1 - SSIM with SSIM averaged over the
+ * 3 H W values, per channel with an 11 x 11 Gaussian window (sigma 1.5), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2. image, target, d_image: planar batch layout of
+ * the frame (device); loss_dev [n_views] overwritten; d_image = dL/dimage
+ * (overwritten). ws: 16-byte aligned, gs_photometric_workspace_size bytes. */
+size_t gs_photometric_workspace_size(const gs_frame_t *frame);
+gs_status_t gs_photometric_loss_grad(const gs_frame_t *frame, const float *image, const float *target,
+                                     float lambda, float *d_image, float *loss_dev, void *ws,
+                                     size_t ws_bytes, gs_stream_t stream);
+
+/* Adam moments per parameter group (device, same shapes as the parameters), in
+ * the order means, log_scales, quats, opacity_logits, sh. */
+typedef struct {
+  float *m[5];
+  float *v[5];
+} gs_adam_state_t;
+
+typedef struct {
+  float lr[5];             /* per group, same order as gs_adam_state_t */
+  float eps;
+  double beta1, beta2;     /* double: 1 - beta2^t is formed on the host, and beta2 in
+                            * FP32 would move it by ~1e-5 relative at t = 3 */
+  int32_t step;            /* 1 for the first step (bias correction) */
+} gs_adam_cfg_t;
+
+/* One Adam step in place: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr / (1 - b1^t) m / (sqrt(v) / sqrt(1 - b2^t) + eps), FP32. If radius is not
+ * NULL ([n_views][n] record radii of the step's projection), rows of Gaussians no
+ * view saw (radius 0 everywhere) are left untouched, moments included ("sparse"
+ * Adam). params: the parameter arrays (updated); sh rows of 3 sh_stride floats. */
+gs_status_t gs_adam_step(const gs_adam_cfg_t *cfg, gs_params_out_t *params, int64_t n, int32_t sh_stride,
+                         const gs_param_grads_t *grads, gs_adam_state_t *state, const int32_t *radius,
+                         int32_t n_views, gs_stream_t stream);
+
+/* Opacity reset of the densification schedule: every opacity logit is lowered to
+ * at most logit(max_opacity); the opacity moments m, v (may be NULL) are cleared. */
+gs_status_t gs_opacity_reset(float *opacity_logits, float *m, float *v, int64_t n, float max_opacity,
+                             gs_stream_t stream);
+
 /* ------------------------------------------------- coarse-to-fine schedule energy */
 /* Sec. "Energy-aware multi-resolution": the downscaling operator D_r (bilinear with
  * anti-aliasing) and the energy ||E(I)||_1 = sum over channels and frequencies of

@@ -65,6 +65,15 @@ class GsParamsOut(C.Structure):
     _fields_ = [("means", vp), ("log_scales", vp), ("quats", vp), ("opacity_logits", vp), ("sh", vp)]
 
 
+class GsAdamState(C.Structure):
+    _fields_ = [("m", vp * 5), ("v", vp * 5)]
+
+
+class GsAdamCfg(C.Structure):
+    _fields_ = [("lr", C.c_float * 5), ("eps", C.c_float), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("step", C.c_int32)]
+
+
 P = C.POINTER
 SIGNATURES = {
     "gs_status_str": (C.c_char_p, [C.c_int]),
@@ -88,6 +97,11 @@ SIGNATURES = {
     "gs_densify_select_static": (C.c_int, [P(GsDensifyCfg), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
     "gs_densify_apply": (C.c_int, [P(GsDensifyCfg), P(GsParams), vp, vp, vp, P(GsParamsOut),
                                    P(GsExtraArray), C.c_int32, C.c_int64, vp, vp, vp, C.c_size_t, vp]),
+    "gs_photometric_workspace_size": (C.c_size_t, [P(GsFrame)]),
+    "gs_photometric_loss_grad": (C.c_int, [P(GsFrame), vp, vp, C.c_float, vp, vp, vp, C.c_size_t, vp]),
+    "gs_adam_step": (C.c_int, [P(GsAdamCfg), P(GsParamsOut), C.c_int64, C.c_int32, P(GsParamGrads),
+                               P(GsAdamState), vp, C.c_int32, vp]),
+    "gs_opacity_reset": (C.c_int, [vp, vp, vp, C.c_int64, C.c_float, vp]),
     "gs_downscaled_size": (C.c_int32, [C.c_int32, C.c_int32]),
     "gs_downscale": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]),
     "gs_spectrum_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
