@@ -8,6 +8,7 @@ accumulated on the way when a DensifyStats object is passed.
 from __future__ import annotations
 
 from dataclasses import dataclass
+from typing import Optional
 
 import torch
 
@@ -18,6 +19,7 @@ from . import rasterizer as R
 class DensifyStats:
     accum: torch.Tensor    # [N] float32
     count: torch.Tensor    # [N] int32
+    radius: Optional[torch.Tensor] = None   # [V * N] int32: the last forward's record radii
 
     @staticmethod
     def zeros(n, device="cuda"):
@@ -33,6 +35,8 @@ class _Rasterize(torch.autograd.Function):
         proj = R.project(params, sh_degree, frame)
         bins = R.bin_sort(proj, frame)
         image, T_final, stop = R.raster_fwd(proj, bins, frame, bg, store_stop=True)
+        if stats is not None:
+            stats.radius = proj.radius
         ctx.save_for_backward(*[params[k] for k in R.PARAM_KEYS])
         ctx.state = (proj, bins, frame, bg, sh_degree, stats, image, stop)
         ctx.mark_non_differentiable(T_final)

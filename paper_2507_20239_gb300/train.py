@@ -4,9 +4,13 @@ framework", "Adaptive Opacity Pruning"), on the library's kernels.
 Every step renders one view at the current stage's resolution through the
 differentiable rasterizer (autograd.rasterize: gs_project -> gs_bin_sort ->
 gs_raster_fwd, backward gs_raster_bwd -> gs_project_bwd with the densification
-statistic fused), takes the L1 loss gradient with gs_l1_loss_grad and updates the
-parameters with Adam (torch.optim.Adam: the optimiser is plumbing here, not a hot-path
-kernel). Every `densify_every` steps inside [densify_from, densify_until] it runs
+statistic fused), takes the gradient of Eq. 3's loss, (1 - lambda) L1 + lambda
+D-SSIM (gs_photometric_loss_grad; lambda = 0 gives the plain L1 of gs_l1_loss_grad),
+and updates the parameters with the fused Adam kernel (gs_adam_step, sparse: only
+Gaussians the view saw). The positional learning rate stays constant while training
+below full resolution and decays log-linearly after (Sec. "Implementation
+details"); the opacities are reset every `opacity_reset_every` steps while
+densifying. Every `densify_every` steps inside [densify_from, densify_until] it runs
 gs_densify_select and gs_densify_apply on the statistics, carrying the Adam moments
 through the compaction (new rows start at zero) and resetting the statistics.
 
@@ -23,6 +27,7 @@ from typing import Callable, Optional
 import numpy as np
 import torch
 
+from . import optim as O
 from . import rasterizer as R
 from .autograd import DensifyStats, rasterize
 
@@ -42,6 +47,10 @@ class Schedule:
     scale_fraction: float = 0.01       # split when the max scale exceeds this fraction of the extent
     prune_tau: float = 0.005
     seed: int = 3
+    ssim_lambda: float = 0.2
+    sparse_adam: bool = True
+    position_lr_final: float = 0.01     # fraction of the initial positional rate reached at the end
+    opacity_reset_every: int = 3000
 
     def stage(self, it):
         cur = self.stages[0]
@@ -73,23 +82,24 @@ class Trainer:
                         for r, (_, tg) in views.items()}
         self.on_densify = on_densify
         self.history = []
+        self.events = []      # per densification: (step, mode, splits, clones, N before, N after)
         self.event = 0
         self._set_params({k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).to(device)
                           for k, v in params.items()}, None)
 
     # ---------------------------------------------------------------- state
-    def _set_params(self, tensors: dict, moments: Optional[dict], step=None):
+    def _set_params(self, tensors: dict, moments: Optional[dict], step=0):
         self.P = {k: tensors[k].contiguous().requires_grad_(True) for k in PARAM_KEYS}
-        self.opt = torch.optim.Adam([{"params": [self.P[k]], "lr": self.lrs[k], "name": k} for k in PARAM_KEYS],
-                                    eps=1e-15)
+        self.opt = O.Adam({k: self.P[k].detach() for k in PARAM_KEYS}, self.lrs)
         if moments is not None:
-            for k in PARAM_KEYS:
-                p = self.P[k]
-                self.opt.state[p] = {"step": step.clone() if torch.is_tensor(step) else torch.tensor(float(step)),
-                                     "exp_avg": moments[k + ".m"].reshape(p.shape).contiguous(),
-                                     "exp_avg_sq": moments[k + ".v"].reshape(p.shape).contiguous()}
+            self.opt.set_moments(moments, self.P)
+            self.opt.t = step
         n = self.P["means"].shape[0]
         self.stats = DensifyStats.zeros(n, self.device)
+
+    def full_res_start(self):
+        return min(s for s, r, _ in self.sched.stages if r == 1) if any(r == 1 for _, r, _ in self.sched.stages) \
+            else self.sched.total
 
     @property
     def n(self):
@@ -104,10 +114,21 @@ class Trainer:
         v = it % len(self.frames[r])
         frame, target = self.frames[r][v], self.targets[r][v]
         image, _ = rasterize(self.P, self.sh_degree(it), frame, stats=self.stats)
-        d_image, loss = R.l1_loss_grad(frame, image.detach(), target)
+        if self.sched.ssim_lambda > 0:
+            d_image, loss = O.photometric_loss_grad(frame, image.detach(), target, self.sched.ssim_lambda)
+        else:
+            d_image, loss = R.l1_loss_grad(frame, image.detach(), target)
         image.backward(d_image)
-        self.opt.step()
-        self.opt.zero_grad(set_to_none=True)
+        lr0 = self.lrs["means"]
+        self.opt.lrs["means"] = lr0 if it <= self.full_res_start() else math.exp(
+            math.log(lr0) + min(1.0, (it - self.full_res_start()) / max(1, self.sched.total - self.full_res_start()))
+            * math.log(self.sched.position_lr_final))
+        grads = {k: self.P[k].grad for k in PARAM_KEYS}
+        with torch.no_grad():
+            self.opt.step({k: self.P[k].detach() for k in PARAM_KEYS}, grads,
+                          radius=self.stats.radius if self.sched.sparse_adam else None, n_views=frame.n_views)
+        for k in PARAM_KEYS:
+            self.P[k].grad = None
         return loss
 
     # ---------------------------------------------------------------- densification
@@ -119,13 +140,8 @@ class Trainer:
                             prune_logit=prune_logit, seed=self.sched.seed, event=self.event)
         P = {k: self.P[k].detach() for k in PARAM_KEYS}
         split, clone, tau, new_n, ws = R.densify_select(cfg, P, self.stats.accum, self.stats.count)
-        extra, step = {}, None
-        for k in PARAM_KEYS:
-            st = self.opt.state.get(self.P[k], {})
-            if "exp_avg" in st:
-                extra[k + ".m"] = st["exp_avg"].reshape(self.n, -1).contiguous()
-                extra[k + ".v"] = st["exp_avg_sq"].reshape(self.n, -1).contiguous()
-                step = st["step"]
+        extra = {k: v.contiguous() for k, v in self.opt.moments().items()}
+        step = self.opt.t
         cap = int(new_n.item())
         out, ex, got_n, err = R.densify_apply(cfg, P, self.sh_degree(it), split, clone, tau, cap, extra=extra,
                                               ws=ws)
@@ -136,14 +152,18 @@ class Trainer:
                                  params=P, accum=self.stats.accum, count=self.stats.count, extra=extra,
                                  split=split, clone=clone, tau=tau, out=out, out_extra=ex, seed=self.sched.seed,
                                  event=self.event))
+        self.events.append((it, int(mode), int(split.sum().item()), int(clone.sum().item()), self.n, cap))
         self.event += 1
-        self._set_params(out, ex if extra else None, step)
+        self._set_params(out, ex, step)
 
     def run(self, log_every: int = 100):
         for it in range(1, self.sched.total + 1):
             loss = self.step(it - 1)
             if self.sched.densify_at(it):
                 self.densify(it)
+            if self.sched.opacity_reset_every and it % self.sched.opacity_reset_every == 0 and \
+                    it <= self.sched.densify_until:
+                O.opacity_reset({k: self.P[k].detach() for k in PARAM_KEYS}, self.opt)
             if it % log_every == 0 or it == self.sched.total:
                 self.history.append((it, self.n, float(loss[0].item())))
         return self.history
@@ -241,7 +261,10 @@ def main(argv=None):
     init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
     tr = Trainer(init, views, sched, extent=1.1 * 4.0)
     hist = tr.run()
-    print(json.dumps({"history": hist, "final_n": tr.n, "init_log_scale": args.init_log_scale,
+    n_split = sum(e[2] for e in tr.events)
+    n_clone = sum(e[3] for e in tr.events)
+    print(json.dumps({"history": hist, "final_n": tr.n, "events": tr.events,
+                      "new_from_clone": n_clone / max(1, n_clone + 2 * n_split), "init_log_scale": args.init_log_scale,
                       "grad_threshold": args.grad_threshold, "energy_schedule": energy}))
 
 
