@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--cpu-sample-tiles", type=int, default=160)
     ap.add_argument("--n", type=int, default=1_500_000)
     ap.add_argument("--tile", default="16x16", help="tile shape WxH (16x16, 8x8, 16x32, 32x16)")
+    ap.add_argument("--backward", choices=["pixel", "splat"], default="pixel",
+                    help="per-pixel gs_raster_bwd or per-splat gs_raster_bwd_splat")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no e2e, batched or CPU legs): for profiler runs")
     return ap.parse_args()
@@ -163,6 +165,25 @@ def measure_capacity(sc, frame, P):
     return M, float(c[0]), float(c[1]), float(stop.double().sum().item())
 
 
+def splat_bucket_stats(step):
+    """Work of the per-splat backward on view 0 from the forward's stop indices:
+    32-entry buckets walked (per tile, up to its largest stop index) and live
+    (pixel, bucket) pairs (per pixel, ceil(stop / 32))."""
+    import torch
+    if step.stop is None:
+        return None
+    f = step.frame
+    tw, th = f.tile
+    st = f.view_pixels(step.stop, 0).to(torch.int64)
+    H, W = st.shape
+    gy, gx = (H + th - 1) // th, (W + tw - 1) // tw
+    pad = torch.zeros(gy * th, gx * tw, dtype=torch.int64, device=st.device)
+    pad[:H, :W] = st
+    tmax = pad.view(gy, th, gx, tw).amax(dim=(1, 3))
+    return {"buckets": int(((tmax + 31) // 32).sum()), "live_pixel_buckets": int(((st + 31) // 32).sum()),
+            "pixels": int(H * W)}
+
+
 def bench_ours(args, rank, local_rank, world):
     import torch
     import torch.distributed as dist
@@ -177,8 +198,8 @@ def bench_ours(args, rank, local_rank, world):
     frame = R.Frame(sc.cameras, tile=tile, device=dev)
     P = R.to_device_params(sc.params(), dev)
     M, p_exam, p_contrib, p_walk_bwd = measure_capacity(sc, frame, P)
-    step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(tile=tile), device=dev,
-                     capacity=int(M * 1.25) + 4096)
+    step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(tile=tile, backward=args.backward),
+                     device=dev, capacity=int(M * 1.25) + 4096)
     for _ in range(max(args.warmup, 3)):
         step.run()
     torch.cuda.synchronize()
@@ -226,7 +247,8 @@ def bench_ours(args, rank, local_rank, world):
         print(json.dumps({"quick": True, "ms_per_step": round(ms, 4), "eager_ms_per_step": round(eager_ms, 4),
                           "stages": stage_ms, "M": M, "pairs_walked_bwd": p_walk_bwd,
                           "pairs_examined": p_exam, "pairs_composited": p_contrib,
-                          "tile_sync": tile_sync_stats(frame, measure_capacity.last_counts)}), flush=True)
+                          "tile_sync": tile_sync_stats(frame, measure_capacity.last_counts),
+                          "splat_buckets": splat_bucket_stats(step)}), flush=True)
         return None
     # ---- end to end: camera + target H2D from pinned memory, loss D2H, every step
     tgt_host = step.target.cpu().pin_memory()

@@ -229,6 +229,37 @@ gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs
                           const gs_raster_cfg_t *cfg, const float *image, const float *d_image,
                           const uint32_t *stop, gs_rec_grads_t *grads, gs_stream_t stream);
 
+/* Per-splat backward (the per-splat parallel back-propagation of the Taming-3DGS
+ * lineage that the paper's base trainer uses; a measured alternative to
+ * gs_raster_bwd, chosen by the autotuner). Same gradient as gs_raster_bwd (up to
+ * summation order), parallel over list entries: each tile's list is cut into
+ * buckets of 32 entries, one lane per entry, and the tile's pixels flow through
+ * each bucket from a checkpoint the forward stored at its first position.
+ *
+ * gs_raster_ckpt_size: bytes of the checkpoint buffer for a frame whose lists hold
+ * at most `capacity` entries (the gs_bins_t capacity): (ceil(capacity / 32) +
+ * n_tiles) * tile_w * tile_h * 16; 0 for an invalid frame or capacity.
+ *
+ * gs_raster_fwd_ckpt: gs_raster_fwd that always writes stop [n_pixels] and also,
+ * for every pixel still compositing at list position 32 b of its tile, the float4
+ * (T, R, G, B) of the state before that position (transmittance and the colour
+ * composited so far) into ckpt. ckpt: device, 16-byte aligned, at least
+ * gs_raster_ckpt_size(frame, bins->capacity) bytes, else GS_ERR_INVALID_ARG;
+ * layout is private to the pair of calls (entries of pixels that had stopped are
+ * left unwritten).
+ *
+ * gs_raster_bwd_splat: gradient of Eq. 2 from the image, stop and ckpt of the
+ * gs_raster_fwd_ckpt call on the same bins; dL/dsigma as in gs_raster_bwd.
+ * OVERWRITES grads (clears, then accumulates once per (tile, list entry)). */
+size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity);
+gs_status_t gs_raster_fwd_ckpt(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
+                               void *ckpt, size_t ckpt_bytes, gs_stream_t stream);
+gs_status_t gs_raster_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                const float *image, const float *d_image, const uint32_t *stop,
+                                const void *ckpt, size_t ckpt_bytes, gs_rec_grads_t *grads,
+                                gs_stream_t stream);
+
 /* Vector-Jacobian product of gs_project: record gradients -> parameter gradients,
  * summed over views (chain rule through the conic inverse, Sigma' = J W Sigma W^T J^T,
  * Sigma = R S S^T R^T, the quaternion normalisation, exp scales, the J clamp, the

@@ -88,6 +88,11 @@ SIGNATURES = {
     "gs_raster_count": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), vp, vp]),
     "gs_l1_loss_grad": (C.c_int, [P(GsFrame), vp, vp, vp, vp, vp]),
     "gs_raster_bwd": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), P(GsRasterCfg), vp, vp, vp, P(GsRecGrads), vp]),
+    "gs_raster_ckpt_size": (C.c_size_t, [P(GsFrame), C.c_int64]),
+    "gs_raster_fwd_ckpt": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), P(GsRasterCfg), vp, vp, vp, vp, C.c_size_t,
+                                     vp]),
+    "gs_raster_bwd_splat": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), vp, vp, vp, vp, C.c_size_t,
+                                      P(GsRecGrads), vp]),
     "gs_project_bwd": (C.c_int, [P(GsParams), P(GsFrame), P(GsProj), P(GsRecGrads), P(GsParamGrads), vp,
                                  vp, vp]),
     "gs_densify_accum": (C.c_int, [vp, vp, P(GsFrame), C.c_int64, vp, vp, vp]),

@@ -2,8 +2,8 @@
 
 For a given scene size and set of view resolutions it times the whole step
 (TrainStep, graph-replayed) for every candidate StepConfig -- tile shape, the
-low tile-id bits the binning sorts while emitting, and the backward's staging
-depth -- and keeps the fastest. None of the knobs changes the rendered images
+low tile-id bits the binning sorts while emitting, the backward's staging
+depth, and the per-pixel or per-splat backward -- and keeps the fastest. None of the knobs changes the rendered images
 (every candidate's images are compared with the first one's); the gradients agree
 up to summation order. Results are cached per (device, Gaussians, SH degree, view
 sizes, candidates) for the life of the process.
@@ -23,11 +23,18 @@ TILES = ((16, 16), (8, 8), (16, 32))
 
 
 def default_candidates(tiles: Sequence = TILES, fused_bits: Sequence = (0, 8),
-                       stage_depths: Sequence = (0, 1)) -> list:
+                       stage_depths: Sequence = (0, 1), splat: bool = True) -> list:
+    """Every (tile, fused bits) pair with each staging depth of the per-pixel
+    backward and, if splat, once with the per-splat backward."""
     out = []
-    for t, f, s in itertools.product(tiles, fused_bits, stage_depths):
-        if lib().gs_tile_supported(int(t[0]), int(t[1])):
-            out.append(StepConfig(tile=(int(t[0]), int(t[1])), sort_fused_bits=int(f), stage_depth=int(s)))
+    for t, f in itertools.product(tiles, fused_bits):
+        if not lib().gs_tile_supported(int(t[0]), int(t[1])):
+            continue
+        tile = (int(t[0]), int(t[1]))
+        for s in stage_depths:
+            out.append(StepConfig(tile=tile, sort_fused_bits=int(f), stage_depth=int(s)))
+        if splat:
+            out.append(StepConfig(tile=tile, sort_fused_bits=int(f), backward="splat"))
     return out
 
 

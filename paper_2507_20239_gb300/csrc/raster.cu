@@ -39,6 +39,15 @@ __device__ __forceinline__ TileCoord tile_coord(const gs_camera_t *cams, int n_v
   return c;
 }
 
+// Checkpoint buckets of the per-splat backward: list positions [32 b, 32 b + 32) of
+// tile t (whose list starts at s_t in the sorted order) own bucket floor(s_t / 32) +
+// t + b. Consecutive tiles' buckets never overlap (floor(s_t / 32) + ceil(len_t / 32)
+// <= floor(s_{t+1} / 32) + 1), so no per-tile scan is needed and, for M listed
+// entries, every bucket is below ceil(M / 32) + n_tiles.
+__device__ __forceinline__ uint64_t ckpt_bucket(uint32_t list_start, uint32_t tile) {
+  return (uint64_t)(list_start >> 5) + tile;
+}
+
 // Pixel mapping: warp w owns the 8x8 block (w % (TW/8), w / (TW/8)) of the tile;
 // lane l owns pixels (2 (l % 4), l / 4) and (2 (l % 4) + 1, l / 4) of that block.
 template <int TW>
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
-    uint32_t *__restrict__ stop_out) {
+    uint32_t *__restrict__ stop_out, float4 *__restrict__ ckpt) {
   constexpr int NW = TW * TH / 64;
   __shared__ float2 s_xy[NW][32];
   __shared__ float4 s_co[NW][32];
@@ -144,6 +153,12 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   }
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
+    if (ckpt) {
+      // state before list position base: (T, accumulated colour) for the per-splat backward
+      float4 *ck = ckpt + (ckpt_bucket(rg.x, blockIdx.x) + (uint64_t)(base >> 5)) * (TW * TH) + ly * TW + lx;
+      if (!done0) ck[0] = make_float4(T0, r0, g0, b0);
+      if (!done1) ck[1] = make_float4(T1, r1, g1, b1);
+    }
     const int j = base + lane;
     const float2 xy = xy_n;
     const float4 co = co_n, c = c_n;
@@ -527,6 +542,150 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
   }
 }
 
+// Per-splat backward (the per-splat parallel back-propagation of the Taming-3DGS
+// lineage that the paper's base trainer uses): the same gradient as
+// raster_bwd_kernel, parallel over list entries instead of pixels. One CTA per tile;
+// warp w takes the tile's 32-entry buckets b = w, w + NW, ... up to the tile's
+// largest stop index, one entry per lane. A bucket's live pixels (stop index beyond
+// its first position) start from the forward's checkpoint (T and the colour
+// composited before the bucket) and flow through the warp diagonally: at step s lane
+// l works on live pixel s - l, taking (T, R) from lane l - 1, which handled that pixel
+// one step earlier, in list order. Each lane sums its entry's moments over the
+// tile's pixels in registers and adds them to the record gradients once, with no
+// cross-lane reduction. Needs the stop indices and the checkpoints written by the
+// forward (gs_raster_fwd_ckpt).
+constexpr int kSplatThreads = 128;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
+    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
+    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
+    int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
+    const uint32_t *__restrict__ stop_in, const float4 *__restrict__ ckpt, float *__restrict__ g_mean2d,
+    float *__restrict__ g_co, float *__restrict__ g_rgb) {
+  constexpr int NP = TW * TH, NW = kSplatThreads / 32;
+  static_assert(NP % 32 == 0, "whole warps of pixels");
+  extern __shared__ float4 s_dyn[];
+  float4 *s_g = s_dyn;                                          // [NP] (dL/dout, <out, dL/dout>)
+  float4 *s_pa = s_g + NP;                                      // [NW][NP] live: (dL/dout, stop bits)
+  float4 *s_pb = s_pa + NW * NP;                                // [NW][NP] live: (x, y, T, R) at bucket start
+  uint32_t *s_stop = reinterpret_cast<uint32_t *>(s_pb + NW * NP);   // [NP]
+  __shared__ uint32_t s_max;
+  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (t == 0) s_max = 0;
+  __syncthreads();
+  {
+    const int64_t plane = (int64_t)tc.W * tc.H;
+    const float *img = image + 3 * tc.pix_off;
+    const float *dim = d_image + 3 * tc.pix_off;
+    uint32_t mx = 0;
+    for (int p = t; p < NP; p += kSplatThreads) {
+      const int px = tc.tx * TW + p % TW, py = tc.ty * TH + p / TW;
+      uint32_t st = 0;
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (px < tc.W && py < tc.H) {
+        const int64_t q = (int64_t)py * tc.W + px;
+        st = stop_in[tc.pix_off + q];
+        g.x = dim[q]; g.y = dim[plane + q]; g.z = dim[2 * plane + q];
+        g.w = g.x * img[q] + g.y * img[plane + q] + g.z * img[2 * plane + q];
+      }
+      s_g[p] = g;
+      s_stop[p] = st;
+      mx = max(mx, st);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) atomicMax(&s_max, mx);
+  }
+  __syncthreads();
+  const uint2 rg = ranges[blockIdx.x];
+  const int n = min((int)(rg.y - rg.x), (int)s_max);
+  const int nb = (n + 31) >> 5;
+  const uint64_t bk0 = ckpt_bucket(rg.x, blockIdx.x);
+  float4 *pa = s_pa + warp * NP, *pb = s_pb + warp * NP;
+  for (int b = warp; b < nb; b += NW) {
+    const int j = 32 * b + lane;   // this lane's list position
+    const bool has = j < n;
+    uint32_t r = 0;
+    float2 xy = make_float2(0.f, 0.f);
+    float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cu = co, c = co;
+    if (has) {
+      r = vals[rg.x + j];
+      xy = mean2d[r];
+      cu = conic_o[r];
+      c = rgb[r];
+      co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
+    }
+    // live pixels, in pixel order: index first, then their data and checkpoint
+    int nl = 0;
+    for (int p0 = 0; p0 < NP; p0 += 32) {
+      const int p = p0 + lane;
+      const bool live = s_stop[p] > (uint32_t)(32 * b);
+      const uint32_t bal = __ballot_sync(0xffffffffu, live);
+      if (live) pa[nl + __popc(bal & lt)].w = __int_as_float(p);
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    const float4 *ck = ckpt + (bk0 + (uint64_t)b) * NP;
+#pragma unroll 4
+    for (int i = lane; i < nl; i += 32) {
+      const int p = __float_as_int(pa[i].w);
+      const float4 k = ck[p];
+      const float4 g = s_g[p];
+      pa[i] = make_float4(g.x, g.y, g.z, __uint_as_float(s_stop[p]));
+      pb[i] = make_float4((float)(tc.tx * TW + p % TW) + 0.5f, (float)(tc.ty * TH + p / TW) + 0.5f, k.x,
+                          g.w - (k.y * g.x + k.z * g.y + k.w * g.z));
+    }
+    __syncwarp();
+    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float T = 1.f, Rr = 0.f;
+    for (int s = 0; s < nl + 31; ++s) {
+      const int i = s - lane;
+      const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
+      const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
+      if (i >= 0 && i < nl) {
+        const float4 q = pb[i];
+        T = lane == 0 ? q.z : Tin;
+        Rr = lane == 0 ? q.w : Rin;
+        if (has) {
+          const float4 g = pa[i];
+          if ((uint32_t)j < __float_as_uint(g.w)) {
+            const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
+            if (f.alpha >= kAlphaMin) {
+              const float one_m = __fsub_rn(1.f, f.alpha);
+              const float w = f.alpha * T;
+              const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
+              Rr = fmaf(-cd, w, Rr);
+              const float dLda = T * cd - __fdividef(Rr, one_m);
+              T = __fmul_rn(T, one_m);
+              v[6] = fmaf(g.x, w, v[6]);
+              v[7] = fmaf(g.y, w, v[7]);
+              v[8] = fmaf(g.z, w, v[8]);
+              const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
+              const float mt = m * f.t, mdy = m * f.dy;
+              v[0] += mt;
+              v[1] += mdy;
+              v[2] = fmaf(mt, f.t, v[2]);
+              v[3] = fmaf(mt, f.dy, v[3]);
+              v[4] = fmaf(mdy, f.dy, v[4]);
+              v[5] += m;
+            }
+          }
+        }
+      }
+    }
+    if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
+                v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
+      const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
+      red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
+      red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
+      red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
+    }
+    __syncwarp();   // the next bucket rewrites this warp's live-pixel arrays
+  }
+}
+
 __global__ void l1_loss_grad_kernel(const gs_camera_t *__restrict__ cams, const float *__restrict__ image,
                                     const float *__restrict__ target, float *__restrict__ d_image, float *loss) {
   const int v = blockIdx.y;
@@ -555,13 +714,13 @@ __global__ void l1_loss_grad_kernel(const gs_camera_t *__restrict__ cams, const 
 template <int TW, int TH, bool COUNT = false>
 static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
-                              cudaStream_t s, uint32_t *counts = nullptr) {
+                              cudaStream_t s, uint32_t *counts = nullptr, float4 *ckpt = nullptr) {
   if (!COUNT) {
     raster_fwd_warp_kernel<TW, TH><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
         reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
         reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
         frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,
-        cfg->store_stop ? stop : nullptr);
+        cfg->store_stop ? stop : nullptr, ckpt);
     GS_LAUNCH_CHECK();
     return GS_OK;
   }
@@ -598,6 +757,36 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
   else
     half ? GS_BWD(false, true) : GS_BWD(false, false);
 #undef GS_BWD
+  GS_LAUNCH_CHECK();
+  return GS_OK;
+}
+
+template <int TW, int TH>
+static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                    const float *image, const float *d_image, const uint32_t *stop,
+                                    const float4 *ckpt, gs_rec_grads_t *g, cudaStream_t s) {
+  const size_t R = (size_t)proj->n_records;
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
+  GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
+  constexpr int NP = TW * TH, NW = kSplatThreads / 32;
+  constexpr size_t smem = (size_t)NP * (sizeof(float4) * (1 + 2 * NW) + sizeof(uint32_t));
+  if (smem > 48 * 1024) {
+    // opt in once per device (not a stream operation, so also safe while a graph is captured)
+    static bool done[64] = {};
+    int dev = 0;
+    GS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GS_ERR_UNSUPPORTED;
+    if (!done[dev]) {
+      GS_CUDA_TRY(cudaFuncSetAttribute(raster_bwd_splat_kernel<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+      done[dev] = true;
+    }
+  }
+  raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles, kSplatThreads, smem, s>>>(
+      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
+      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
+      frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
@@ -643,6 +832,58 @@ extern "C" gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bin
   if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd<8, 8>(proj, bins, frame, image, d_image, stop, half, grads, s);
   if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd<16, 32>(proj, bins, frame, image, d_image, stop, half, grads, s);
   if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd<32, 16>(proj, bins, frame, image, d_image, stop, half, grads, s);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity) {
+  if (!frame || capacity < 0 || frame->n_tiles <= 0 || !gs_tile_supported(frame->tile_w, frame->tile_h)) return 0;
+  const uint64_t buckets = ((uint64_t)capacity + 31u) / 32u + (uint64_t)frame->n_tiles;
+  return (size_t)(buckets * (uint64_t)frame->tile_w * (uint64_t)frame->tile_h * sizeof(float4));
+}
+
+extern "C" gs_status_t gs_raster_fwd_ckpt(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                          const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
+                                          void *ckpt, size_t ckpt_bytes, gs_stream_t stream) {
+  if (!proj || !bins || !frame || !cfg || !image || !T_final || !stop || !ckpt || !frame->cams_dev ||
+      frame->n_tiles <= 0)
+    return GS_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->ranges || !proj->mean2d || !a16(proj->conic_opacity) || !a16(proj->rgb) || !a16(ckpt))
+    return GS_ERR_INVALID_ARG;
+  const size_t need = gs_raster_ckpt_size(frame, bins->capacity);
+  if (need == 0) return GS_ERR_UNSUPPORTED;
+  if (ckpt_bytes < need) return GS_ERR_INVALID_ARG;
+  gs_raster_cfg_t c = *cfg;
+  c.store_stop = 1;
+  cudaStream_t s = as_stream(stream);
+  float4 *ck = static_cast<float4 *>(ckpt);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_fwd<16, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_fwd<8, 8>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_fwd<16, 32>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_fwd<32, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
+  return GS_ERR_UNSUPPORTED;
+}
+
+extern "C" gs_status_t gs_raster_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
+                                           const float *image, const float *d_image, const uint32_t *stop,
+                                           const void *ckpt, size_t ckpt_bytes, gs_rec_grads_t *grads,
+                                           gs_stream_t stream) {
+  if (!proj || !bins || !frame || !image || !d_image || !stop || !ckpt || !grads || !frame->cams_dev ||
+      frame->n_tiles <= 0)
+    return GS_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->ranges || !a16(proj->conic_opacity) || !a16(proj->rgb) || !a16(ckpt))
+    return GS_ERR_INVALID_ARG;
+  if (!grads->d_mean2d || !a16(grads->d_conic_opacity) || !a16(grads->d_rgb) || !grads->d_conic_opacity ||
+      !grads->d_rgb || ((reinterpret_cast<uintptr_t>(grads->d_mean2d) & 7u) != 0))
+    return GS_ERR_INVALID_ARG;
+  const size_t need = gs_raster_ckpt_size(frame, bins->capacity);
+  if (need == 0) return GS_ERR_UNSUPPORTED;
+  if (ckpt_bytes < need) return GS_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const float4 *ck = static_cast<const float4 *>(ckpt);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd_splat<16, 16>(proj, bins, frame, image, d_image, stop, ck, grads, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd_splat<8, 8>(proj, bins, frame, image, d_image, stop, ck, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd_splat<16, 32>(proj, bins, frame, image, d_image, stop, ck, grads, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd_splat<32, 16>(proj, bins, frame, image, d_image, stop, ck, grads, s);
   return GS_ERR_UNSUPPORTED;
 }
 

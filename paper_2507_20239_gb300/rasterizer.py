@@ -247,6 +247,34 @@ def raster_fwd(proj: Projected, bins: Bins, frame: Frame, bg=(0.0, 0.0, 0.0), st
     return image, T_final, (stop if store_stop else None)
 
 
+def ckpt_bytes(frame: Frame, capacity: int) -> int:
+    """Bytes of the per-splat backward's checkpoint buffer for lists of at most
+    `capacity` entries on this frame."""
+    n = int(lib().gs_raster_ckpt_size(C.byref(frame.frame), int(capacity)))
+    if n == 0:
+        raise _abi.GsError(1, f"gs_raster_ckpt_size (frame or capacity {capacity})")
+    return n
+
+
+def alloc_ckpt(frame: Frame, bins: "Bins") -> torch.Tensor:
+    """Checkpoint buffer (uint8, 16-byte aligned) for raster_fwd_ckpt on these bins."""
+    return torch.empty(ckpt_bytes(frame, bins.capacity), dtype=torch.uint8, device=frame.device)
+
+
+def raster_fwd_ckpt(proj: Projected, bins: Bins, frame: Frame, ckpt: torch.Tensor, bg=(0.0, 0.0, 0.0),
+                    image=None, T_final=None, stop=None, stream=None):
+    """raster_fwd with stop indices and the per-splat backward's checkpoints."""
+    dev = frame.device
+    image = torch.empty(3 * frame.n_pixels, dtype=torch.float32, device=dev) if image is None else image
+    T_final = torch.empty(frame.n_pixels, dtype=torch.float32, device=dev) if T_final is None else T_final
+    stop = torch.empty(frame.n_pixels, dtype=torch.int32, device=dev) if stop is None else stop
+    cfg = raster_cfg(bg, True)
+    check(lib().gs_raster_fwd_ckpt(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame),
+                                   C.byref(cfg), _p(image), _p(T_final), _p(stop), _p(ckpt),
+                                   ckpt.numel() * ckpt.element_size(), _stream(stream)), "gs_raster_fwd_ckpt")
+    return image, T_final, stop
+
+
 def raster_count(proj: Projected, bins: Bins, frame: Frame, counts=None, stream=None):
     """Per-pixel (entries examined, entries composited) of Eq. 2 -> int32 [n_pixels, 2]."""
     counts = torch.empty(frame.n_pixels, 2, dtype=torch.int32, device=frame.device) if counts is None else counts
@@ -374,3 +402,14 @@ def densify_apply(cfg: _abi.GsDensifyCfg, params: dict, sh_degree: int, split, c
                                  len(extra), int(capacity), _p(new_n), _p(err), _p(ws), ws.numel(),
                                  _stream(stream)), "gs_densify_apply")
     return out, ex_out, new_n, err
+
+
+def raster_bwd_splat(proj: Projected, bins: Bins, frame: Frame, image, d_image, stop, ckpt,
+                     grads: Optional[RecGrads] = None, stream=None) -> RecGrads:
+    """Per-splat backward from raster_fwd_ckpt's image, stop indices and checkpoints."""
+    grads = RecGrads.zeros(proj.mean2d.shape[0], frame.device) if grads is None else grads
+    check(lib().gs_raster_bwd_splat(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame),
+                                    _p(image), _p(_need(d_image, torch.float32, "d_image")), _p(stop), _p(ckpt),
+                                    ckpt.numel() * ckpt.element_size(), C.byref(grads.struct()),
+                                    _stream(stream)), "gs_raster_bwd_splat")
+    return grads

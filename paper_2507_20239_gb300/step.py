@@ -2,10 +2,11 @@
 
 TrainStep runs, on the current stream: gs_project -> gs_bin_sort -> gs_raster_fwd
 (Eq. 2) -> gs_l1_loss_grad (the L1 term of Eq. 3) -> gs_raster_bwd ->
-gs_project_bwd (parameter gradients and the densification statistic). With
-store_stop the forward stores each pixel's stop index and the backward walks only
-up to it; without, no per-pixel index is kept and the backward recomputes the
-cut-off (4 bytes per pixel less). No count returns to the host inside run(), so
+gs_project_bwd (parameter gradients and the densification statistic); with the
+per-splat backward, gs_raster_fwd_ckpt and gs_raster_bwd_splat take the raster
+stages. With store_stop the forward stores each pixel's stop index and the
+backward walks only up to it; without, no per-pixel index is kept and the
+backward recomputes the cut-off (4 bytes per pixel less). No count returns to the host inside run(), so
 the sequence can be captured once into a CUDA graph (capture()) and replayed.
 
 The duplicate capacity of the per-tile lists is sized from a measured M with
@@ -22,17 +23,30 @@ from . import rasterizer as R
 from .autograd import DensifyStats
 
 
+BACKWARDS = ("pixel", "splat")
+
+
 @dataclass(frozen=True)
 class StepConfig:
     """Tuning knobs of one step (none changes the images; gradients agree up to
     summation order): tile shape, low tile-id bits sorted during emission
-    (0 = the library's choice) and the backward's staging depth (0 = one list entry
-    per thread per CTA step, 1 = half as many)."""
+    (0 = the library's choice), the backward's staging depth (0 = one list entry
+    per thread per CTA step, 1 = half as many) and the backward itself ("pixel":
+    gs_raster_bwd, parallel over pixels; "splat": gs_raster_bwd_splat, parallel over
+    list entries from checkpoints the forward stores; the staging depth does not
+    apply to it)."""
     tile: tuple = (16, 16)
     sort_fused_bits: int = 0
     stage_depth: int = 0
+    backward: str = "pixel"
+
+    def __post_init__(self):
+        if self.backward not in BACKWARDS:
+            raise ValueError(f"backward must be one of {BACKWARDS}, not {self.backward!r}")
 
     def label(self) -> str:
+        if self.backward == "splat":
+            return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/splat"
         return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/s{self.stage_depth}"
 
 
@@ -47,7 +61,8 @@ class TrainStep:
     def __init__(self, params: dict, sh_degree: int, cameras, target_images, config: StepConfig = StepConfig(),
                  device="cuda", capacity: int | None = None, headroom: float = 1.25, store_stop: bool = True):
         self.P, self.sh_degree, self.config = params, int(sh_degree), config
-        self.store_stop = bool(store_stop)
+        self.splat = config.backward == "splat"
+        self.store_stop = bool(store_stop) or self.splat   # the per-splat backward needs the stop indices
         self.frame = R.Frame(cameras, tile=config.tile, device=device, sort_fused_bits=config.sort_fused_bits)
         f = self.frame
         n = params["means"].shape[0]
@@ -58,7 +73,8 @@ class TrainStep:
         self.bins = R.alloc_bins(f, Rn, capacity)
         self.image = torch.empty(3 * f.n_pixels, device=f.device)
         self.T = torch.empty(f.n_pixels, device=f.device)
-        self.stop = torch.empty(f.n_pixels, dtype=torch.int32, device=f.device) if store_stop else None
+        self.stop = torch.empty(f.n_pixels, dtype=torch.int32, device=f.device) if self.store_stop else None
+        self.ckpt = R.alloc_ckpt(f, self.bins) if self.splat else None
         self.d_image = torch.empty_like(self.image)
         self.loss = torch.empty(f.n_views, device=f.device)
         self.target = f.pack_images(target_images).contiguous()
@@ -76,13 +92,20 @@ class TrainStep:
         rec(1)
         R.bin_sort_into(self.proj, f, self.bins)
         rec(2)
-        R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T, store_stop=self.store_stop,
-                     stop=self.stop)
+        if self.splat:
+            R.raster_fwd_ckpt(self.proj, self.bins, f, self.ckpt, image=self.image, T_final=self.T, stop=self.stop)
+        else:
+            R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T, store_stop=self.store_stop,
+                         stop=self.stop)
         rec(3)
         R.l1_loss_grad(f, self.image, self.target, d_image=self.d_image, loss=self.loss)
         rec(4)
-        R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec, stop=self.stop,
-                     stage_depth=cfg.stage_depth)
+        if self.splat:
+            R.raster_bwd_splat(self.proj, self.bins, f, self.image, self.d_image, self.stop, self.ckpt,
+                               grads=self.rec)
+        else:
+            R.raster_bwd(self.proj, self.bins, f, self.image, self.d_image, grads=self.rec, stop=self.stop,
+                         stage_depth=cfg.stage_depth)
         rec(5)
         R.project_bwd(self.P, self.sh_degree, f, self.proj, self.rec, out=self.pgrads,
                       accum=self.stats.accum, count=self.stats.count)

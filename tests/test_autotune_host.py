@@ -43,5 +43,16 @@ def test_fused_bits_must_fit_the_tile_ids():
 def test_default_candidates_cover_the_tile_shapes():
     c = at.default_candidates()
     assert {x.tile for x in c} == {(16, 16), (8, 8), (16, 32)}
-    assert {x.stage_depth for x in c} == {0, 1}
-    assert len(set(c)) == len(c) == 12
+    assert {x.stage_depth for x in c if x.backward == "pixel"} == {0, 1}
+    # per (tile, fused bits): two per-pixel staging depths and the per-splat backward
+    assert sum(x.backward == "splat" for x in c) == 6
+    assert len(set(c)) == len(c) == 18
+    assert len({x.label() for x in c}) == 18
+    assert len(at.default_candidates(splat=False)) == 12
+
+
+def test_step_config_backward_is_validated():
+    assert StepConfig((8, 8), 2, 0, "splat").label() == "8x8/f2/splat"
+    assert StepConfig((16, 16), 0, 1).label() == "16x16/f0/s1"
+    with pytest.raises(ValueError):
+        StepConfig(backward="tile")

@@ -1,6 +1,7 @@
 """The step's tuning knobs and the autotuner that picks them (tile shape, tile-id
-bits sorted during emission, the backward's staging depth): none changes the
-rendered images, and the gradients agree up to summation order."""
+bits sorted during emission, the backward's staging depth, per-pixel or per-splat
+backward): none changes the rendered images, and the gradients agree up to
+summation order."""
 import numpy as np
 import pytest
 import torch
@@ -26,7 +27,7 @@ def test_knobs_keep_images_and_gradients():
     P = dev_params(sc)
     ref = _run(sc, P, StepConfig())
     cands = default_candidates(tiles=((16, 16), (8, 8), (16, 32)), fused_bits=(0, 2, 8), stage_depths=(0, 1))
-    assert len(cands) == 18
+    assert len(cands) == 27          # 9 (tile, bits) pairs x (two staging depths + per-splat)
     for cfg in cands + ["recomputed"]:
         st = _run(sc, P, StepConfig(), store_stop=False) if cfg == "recomputed" else _run(sc, P, cfg)
         for v in range(len(sc.cameras)):
@@ -41,7 +42,14 @@ def test_knobs_keep_images_and_gradients():
         # and not another; it never touches a pixel and gets a zero gradient
         if st.config.tile == ref.config.tile:
             assert torch.equal(st.stats.count, ref.stats.count), cfg
-        assert torch.allclose(st.stats.accum, ref.stats.accum, rtol=1e-4, atol=1e-9), cfg
+        # the statistic is a per-Gaussian norm of a sum of per-pixel terms that can
+        # cancel; summed in another order (the per-splat backward also starts each
+        # 32-entry bucket from the forward's checkpoint) a small one moves by more
+        # than 1e-4 of itself, so it is held like the gradients: relative L2, and
+        # element-wise against the largest value
+        a, b = st.stats.accum.double(), ref.stats.accum.double()
+        assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-4, cfg
+        assert torch.all((a - b).abs() <= 1e-4 * b.abs() + 1e-5 * b.abs().max()), cfg
 
 
 def test_autotune_picks_a_measured_candidate():
