@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
                                                        const gs_camera_t *__restrict__ cams, int n_views,
                                                        int64_t n_per_view, int tw, int th, int fbits,
                                                        uint32_t *__restrict__ hist, BinRec *__restrict__ brec,
-                                                       uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals) {
+                                                       uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
+                                                       uint32_t *work) {
   __shared__ BinRec s_rec[8][32];
   __shared__ uint2 s_unit[8][kUnits];            // (record slot << 24 | run length, tile id of the run's first column)
   __shared__ uint32_t s_hpre[8][kUnits + 1];     // exclusive scan of the run lengths
@@ -289,9 +290,14 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
   const uint32_t nd = 1u << fbits, dmask = nd - 1u;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; k0 < nv; k0 += nw * 32) {
-    const uint32_t batch = k0 / 32u;
+  // batches are claimed one at a time from a counter (zeroed before the launch):
+  // their hit counts vary widely, so a fixed assignment leaves SMs idle at the end
+  for (;;) {
+    uint32_t batch = 0;
+    if (lane == 0) batch = atomicAdd(work, 1u);
+    batch = __shfl_sync(0xffffffffu, batch, 0);
+    if (batch >= NB) break;
+    const uint32_t k0 = batch * 32u;
     for (uint32_t d = lane; d < nd; d += 32) s_cur[wib][d] = EMIT ? hist[(uint64_t)d * NB + batch] : 0u;
     // this lane's record: constants to shared memory, its row count to the scan
     uint32_t nrow = 0;
@@ -477,7 +483,8 @@ struct BinWs {
   uint32_t *dk0, *dk1, *dv1;         // duplicate tile keys (double buffered) + second value buffer
   uint64_t *block_sums;
   uint32_t *hist;
-  uint32_t *counters;                // [0] n_vis, [1] M, [2] overflow
+  uint32_t *counters;                // [0] n_vis, [1] M, [2] overflow, [3] [4] batch counters of the
+                                     // counting and the emitting pass
   size_t bytes;
 };
 
@@ -620,7 +627,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int eg = num_sms() * 8;
   bin_rows_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
                                               n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
-                                              nullptr, nullptr);
+                                              nullptr, nullptr, w.counters + 3);
   GS_LAUNCH_CHECK();
   HistScan hs{w.dhist, n_vis, fbits, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
   if (gs_status_t st = run_scan(hs, w.block_sums, G, s)) return st;
@@ -631,7 +638,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const bool emit_to_A = (passes % 2) == 0;
   bin_rows_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
-                                             emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v);
+                                             emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v, w.counters + 4);
   GS_LAUNCH_CHECK();
   // 5. stable sort by the remaining tile-id bits
   bool res0 = true;

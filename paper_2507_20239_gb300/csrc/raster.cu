@@ -113,7 +113,7 @@ __device__ __forceinline__ int warp_select(const float4 *s_rgb, int cnt, int war
 // stages it in the warp's shared slots if it passes; the warp then composites the
 // passing entries in list order. A warp leaves as soon as its 64 pixels have
 // stopped, so neither barriers nor finished neighbours hold it.
-template <int TW, int TH>
+template <int TW, int TH, bool CKPT>
 __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   }
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
-    if (ckpt) {
+    if (CKPT) {
       // state before list position base: (T, accumulated colour) for the per-splat backward
       float4 *ck = ckpt + (ckpt_bucket(rg.x, blockIdx.x) + (uint64_t)(base >> 5)) * (TW * TH) + ly * TW + lx;
       if (!done0) ck[0] = make_float4(T0, r0, g0, b0);
@@ -566,15 +566,19 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
   constexpr int NP = TW * TH, NW = kSplatThreads / 32;
   static_assert(NP % 32 == 0, "whole warps of pixels");
   extern __shared__ float4 s_dyn[];
+  constexpr int NL = NP + 32;                                   // live entries per warp (+ 32 stopped)
   float4 *s_g = s_dyn;                                          // [NP] (dL/dout, <out, dL/dout>)
-  float4 *s_pa = s_g + NP;                                      // [NW][NP] live: (dL/dout, stop bits)
-  float4 *s_pb = s_pa + NW * NP;                                // [NW][NP] live: (x, y, T, R) at bucket start
-  uint32_t *s_stop = reinterpret_cast<uint32_t *>(s_pb + NW * NP);   // [NP]
-  __shared__ uint32_t s_max;
+  float4 *s_pa = s_g + NP;                                      // [NW][NL] live: (dL/dout, stop bits)
+  float4 *s_pb = s_pa + NW * NL;                                // [NW][NL] live: (x, y, T, R) at bucket start
+  uint32_t *s_stop = reinterpret_cast<uint32_t *>(s_pb + NW * NL);   // [NP]
+  __shared__ uint32_t s_max, s_next;
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  if (t == 0) s_max = 0;
+  if (t == 0) {
+    s_max = 0;
+    s_next = NW;
+  }
   __syncthreads();
   {
     const int64_t plane = (int64_t)tc.W * tc.H;
@@ -603,8 +607,10 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
   const int n = min((int)(rg.y - rg.x), (int)s_max);
   const int nb = (n + 31) >> 5;
   const uint64_t bk0 = ckpt_bucket(rg.x, blockIdx.x);
-  float4 *pa = s_pa + warp * NP, *pb = s_pb + warp * NP;
-  for (int b = warp; b < nb; b += NW) {
+  float4 *pa = s_pa + warp * NL, *pb = s_pb + warp * NL;
+  // bucket b = warp first, then the next unclaimed one (earlier buckets hold more
+  // live pixels, so a fixed round robin would load the warps unevenly)
+  for (int b = warp; b < nb;) {
     const int j = 32 * b + lane;   // this lane's list position
     const bool has = j < n;
     uint32_t r = 0;
@@ -617,7 +623,9 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       c = rgb[r];
       co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
     }
-    // live pixels, in pixel order: index first, then their data and checkpoint
+    // live pixels, in pixel order: index first, then their data and checkpoint;
+    // 32 entries past the last one read as stopped (stop 0), so lanes whose pixel
+    // index ran past the list need no bounds test
     int nl = 0;
     for (int p0 = 0; p0 < NP; p0 += 32) {
       const int p = p0 + lane;
@@ -637,42 +645,43 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       pb[i] = make_float4((float)(tc.tx * TW + p % TW) + 0.5f, (float)(tc.ty * TH + p / TW) + 0.5f, k.x,
                           g.w - (k.y * g.x + k.z * g.y + k.w * g.z));
     }
+    pa[nl + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pb[nl + lane] = make_float4(0.f, 0.f, 1.f, 0.f);
     __syncwarp();
     float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float T = 1.f, Rr = 0.f;
+    const uint32_t jj = (uint32_t)j;
+#pragma unroll 2
     for (int s = 0; s < nl + 31; ++s) {
       const int i = s - lane;
+      const int ic = max(i, 0);
       const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
       const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
-      if (i >= 0 && i < nl) {
-        const float4 q = pb[i];
-        T = lane == 0 ? q.z : Tin;
-        Rr = lane == 0 ? q.w : Rin;
-        if (has) {
-          const float4 g = pa[i];
-          if ((uint32_t)j < __float_as_uint(g.w)) {
-            const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
-            if (f.alpha >= kAlphaMin) {
-              const float one_m = __fsub_rn(1.f, f.alpha);
-              const float w = f.alpha * T;
-              const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
-              Rr = fmaf(-cd, w, Rr);
-              const float dLda = T * cd - __fdividef(Rr, one_m);
-              T = __fmul_rn(T, one_m);
-              v[6] = fmaf(g.x, w, v[6]);
-              v[7] = fmaf(g.y, w, v[7]);
-              v[8] = fmaf(g.z, w, v[8]);
-              const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
-              const float mt = m * f.t, mdy = m * f.dy;
-              v[0] += mt;
-              v[1] += mdy;
-              v[2] = fmaf(mt, f.t, v[2]);
-              v[3] = fmaf(mt, f.dy, v[3]);
-              v[4] = fmaf(mdy, f.dy, v[4]);
-              v[5] += m;
-            }
-          }
-        }
+      const float4 q = pb[ic];
+      const float4 g = pa[ic];
+      T = lane == 0 ? q.z : Tin;
+      Rr = lane == 0 ? q.w : Rin;
+      // list position before the pixel's stop (false past the live list and for lanes
+      // without an entry, since every stop index is at most the list length)
+      const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
+      if (i >= 0 && jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
+        const float one_m = __fsub_rn(1.f, f.alpha);
+        const float w = f.alpha * T;
+        const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
+        Rr = fmaf(-cd, w, Rr);
+        const float dLda = T * cd - __fdividef(Rr, one_m);
+        T = __fmul_rn(T, one_m);
+        v[6] = fmaf(g.x, w, v[6]);
+        v[7] = fmaf(g.y, w, v[7]);
+        v[8] = fmaf(g.z, w, v[8]);
+        const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
+        const float mt = m * f.t, mdy = m * f.dy;
+        v[0] += mt;
+        v[1] += mdy;
+        v[2] = fmaf(mt, f.t, v[2]);
+        v[3] = fmaf(mt, f.dy, v[3]);
+        v[4] = fmaf(mdy, f.dy, v[4]);
+        v[5] += m;
       }
     }
     if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
@@ -683,6 +692,9 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
     }
     __syncwarp();   // the next bucket rewrites this warp's live-pixel arrays
+    uint32_t nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&s_next, 1u);
+    b = (int)__shfl_sync(0xffffffffu, nxt, 0);
   }
 }
 
@@ -716,11 +728,14 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
                               cudaStream_t s, uint32_t *counts = nullptr, float4 *ckpt = nullptr) {
   if (!COUNT) {
-    raster_fwd_warp_kernel<TW, TH><<<frame->n_tiles, TW * TH / 2, 0, s>>>(
-        reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
-        reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
-        frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,
-        cfg->store_stop ? stop : nullptr, ckpt);
+#define GS_FWD(CK)                                                                                           \
+  raster_fwd_warp_kernel<TW, TH, CK><<<frame->n_tiles, TW * TH / 2, 0, s>>>(                                  \
+      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),   \
+      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),  \
+      frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,                    \
+      cfg->store_stop ? stop : nullptr, ckpt)
+    ckpt ? GS_FWD(true) : GS_FWD(false);
+#undef GS_FWD
     GS_LAUNCH_CHECK();
     return GS_OK;
   }
@@ -770,7 +785,7 @@ static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
   constexpr int NP = TW * TH, NW = kSplatThreads / 32;
-  constexpr size_t smem = (size_t)NP * (sizeof(float4) * (1 + 2 * NW) + sizeof(uint32_t));
+  constexpr size_t smem = (size_t)NP * (sizeof(float4) + sizeof(uint32_t)) + (size_t)2 * NW * (NP + 32) * sizeof(float4);
   if (smem > 48 * 1024) {
     // opt in once per device (not a stream operation, so also safe while a graph is captured)
     static bool done[64] = {};
