@@ -545,16 +545,20 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
 // Per-splat backward (the per-splat parallel back-propagation of the Taming-3DGS
 // lineage that the paper's base trainer uses): the same gradient as
 // raster_bwd_kernel, parallel over list entries instead of pixels. One CTA per tile;
-// warp w takes the tile's 32-entry buckets b = w, w + NW, ... up to the tile's
-// largest stop index, one entry per lane. A bucket's live pixels (stop index beyond
-// its first position) start from the forward's checkpoint (T and the colour
-// composited before the bucket) and flow through the warp diagonally: at step s lane
-// l works on live pixel s - l, taking (T, R) from lane l - 1, which handled that pixel
-// one step earlier, in list order. Each lane sums its entry's moments over the
-// tile's pixels in registers and adds them to the record gradients once, with no
-// cross-lane reduction. Needs the stop indices and the checkpoints written by the
-// forward (gs_raster_fwd_ckpt).
+// its warps claim the tile's 32-entry buckets (up to the tile's largest stop index)
+// one at a time, one entry per lane. A bucket's live pixels (stop index beyond its
+// first position) start from the forward's checkpoint (T and the colour composited
+// before the bucket) and flow through the warp diagonally: at step s lane l works on
+// live pixel s - l, taking (T, R) from lane l - 1, which handled that pixel one step
+// earlier, in list order. Each lane sums its entry's moments over the tile's pixels
+// in registers and adds them to the record gradients once, with no cross-lane
+// reduction. Since the lanes only ever read 32 consecutive live pixels, a warp keeps
+// them in a 64-slot ring refilled every 32 steps (the next 32 pixels' checkpoints are
+// loaded meanwhile), which keeps shared memory per CTA small and occupancy high.
+// Needs the stop indices and the checkpoints written by the forward
+// (gs_raster_fwd_ckpt).
 constexpr int kSplatThreads = 128;
+constexpr int kSplatRing = 64;
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
@@ -564,13 +568,12 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
     const uint32_t *__restrict__ stop_in, const float4 *__restrict__ ckpt, float *__restrict__ g_mean2d,
     float *__restrict__ g_co, float *__restrict__ g_rgb) {
   constexpr int NP = TW * TH, NW = kSplatThreads / 32;
-  static_assert(NP % 32 == 0, "whole warps of pixels");
-  extern __shared__ float4 s_dyn[];
-  constexpr int NL = NP + 32;                                   // live entries per warp (+ 32 stopped)
-  float4 *s_g = s_dyn;                                          // [NP] (dL/dout, <out, dL/dout>)
-  float4 *s_pa = s_g + NP;                                      // [NW][NL] live: (dL/dout, stop bits)
-  float4 *s_pb = s_pa + NW * NL;                                // [NW][NL] live: (x, y, T, R) at bucket start
-  uint32_t *s_stop = reinterpret_cast<uint32_t *>(s_pb + NW * NL);   // [NP]
+  static_assert(NP % 32 == 0 && NP <= 65536, "whole warps of pixels, 16-bit indices");
+  __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
+  __shared__ uint32_t s_stop[NP];
+  __shared__ uint16_t s_live[NW][NP];              // the bucket's live pixels, in pixel order
+  __shared__ float4 s_ra[NW][kSplatRing];          // ring: (dL/dout, stop bits) of live pixel i at i % 64
+  __shared__ float4 s_rb[NW][kSplatRing];          // ring: (x, y, T, R) at the bucket start
   __shared__ uint32_t s_max, s_next;
   const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -607,7 +610,8 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
   const int n = min((int)(rg.y - rg.x), (int)s_max);
   const int nb = (n + 31) >> 5;
   const uint64_t bk0 = ckpt_bucket(rg.x, blockIdx.x);
-  float4 *pa = s_pa + warp * NL, *pb = s_pb + warp * NL;
+  uint16_t *live = s_live[warp];
+  float4 *ra = s_ra[warp], *rb = s_rb[warp];
   // bucket b = warp first, then the next unclaimed one (earlier buckets hold more
   // live pixels, so a fixed round robin would load the warps unevenly)
   for (int b = warp; b < nb;) {
@@ -623,66 +627,78 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       c = rgb[r];
       co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
     }
-    // live pixels, in pixel order: index first, then their data and checkpoint;
-    // 32 entries past the last one read as stopped (stop 0), so lanes whose pixel
-    // index ran past the list need no bounds test
     int nl = 0;
     for (int p0 = 0; p0 < NP; p0 += 32) {
       const int p = p0 + lane;
-      const bool live = s_stop[p] > (uint32_t)(32 * b);
-      const uint32_t bal = __ballot_sync(0xffffffffu, live);
-      if (live) pa[nl + __popc(bal & lt)].w = __int_as_float(p);
+      const bool on = s_stop[p] > (uint32_t)(32 * b);
+      const uint32_t bal = __ballot_sync(0xffffffffu, on);
+      if (on) live[nl + __popc(bal & lt)] = (uint16_t)p;
       nl += __popc(bal);
     }
     __syncwarp();
     const float4 *ck = ckpt + (bk0 + (uint64_t)b) * NP;
-#pragma unroll 4
-    for (int i = lane; i < nl; i += 32) {
-      const int p = __float_as_int(pa[i].w);
-      const float4 k = ck[p];
-      const float4 g = s_g[p];
-      pa[i] = make_float4(g.x, g.y, g.z, __uint_as_float(s_stop[p]));
-      pb[i] = make_float4((float)(tc.tx * TW + p % TW) + 0.5f, (float)(tc.ty * TH + p / TW) + 0.5f, k.x,
-                          g.w - (k.y * g.x + k.z * g.y + k.w * g.z));
-    }
-    pa[nl + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    pb[nl + lane] = make_float4(0.f, 0.f, 1.f, 0.f);
-    __syncwarp();
+    // live pixel `slot` for this lane: its index (-1 past the list) and checkpoint
+    int pn = -1;
+    float4 kn = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto fetch = [&](int slot) {
+      pn = slot < nl ? (int)live[slot] : -1;
+      if (pn >= 0) kn = ck[pn];
+    };
+    fetch(lane);
     float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float T = 1.f, Rr = 0.f;
     const uint32_t jj = (uint32_t)j;
-#pragma unroll 2
-    for (int s = 0; s < nl + 31; ++s) {
-      const int i = s - lane;
-      const int ic = max(i, 0);
-      const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
-      const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
-      const float4 q = pb[ic];
-      const float4 g = pa[ic];
-      T = lane == 0 ? q.z : Tin;
-      Rr = lane == 0 ? q.w : Rin;
-      // list position before the pixel's stop (false past the live list and for lanes
-      // without an entry, since every stop index is at most the list length)
-      const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
-      if (i >= 0 && jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
-        const float one_m = __fsub_rn(1.f, f.alpha);
-        const float w = f.alpha * T;
-        const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
-        Rr = fmaf(-cd, w, Rr);
-        const float dLda = T * cd - __fdividef(Rr, one_m);
-        T = __fmul_rn(T, one_m);
-        v[6] = fmaf(g.x, w, v[6]);
-        v[7] = fmaf(g.y, w, v[7]);
-        v[8] = fmaf(g.z, w, v[8]);
-        const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
-        const float mt = m * f.t, mdy = m * f.dy;
-        v[0] += mt;
-        v[1] += mdy;
-        v[2] = fmaf(mt, f.t, v[2]);
-        v[3] = fmaf(mt, f.dy, v[3]);
-        v[4] = fmaf(mdy, f.dy, v[4]);
-        v[5] += m;
+    for (int s0 = 0; s0 < nl + 31; s0 += 32) {
+      {
+        // ring slots s0 .. s0 + 31 (those of s0 - 64 .. s0 - 33 are no longer read);
+        // past the list a slot reads as stopped (stop 0)
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (pn >= 0) {
+          const float4 g = s_g[pn];
+          A = make_float4(g.x, g.y, g.z, __uint_as_float(s_stop[pn]));
+          B = make_float4((float)(tc.tx * TW + pn % TW) + 0.5f, (float)(tc.ty * TH + pn / TW) + 0.5f, kn.x,
+                          g.w - (kn.y * g.x + kn.z * g.y + kn.w * g.z));
+        }
+        ra[(s0 + lane) & (kSplatRing - 1)] = A;
+        rb[(s0 + lane) & (kSplatRing - 1)] = B;
+        fetch(s0 + 32 + lane);
+        __syncwarp();
       }
+      const int s1 = min(s0 + 32, nl + 31);
+#pragma unroll 2
+      for (int s = s0; s < s1; ++s) {
+        const int i = s - lane;
+        const int ic = max(i, 0) & (kSplatRing - 1);
+        const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
+        const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
+        const float4 q = rb[ic];
+        const float4 g = ra[ic];
+        T = lane == 0 ? q.z : Tin;
+        Rr = lane == 0 ? q.w : Rin;
+        // a list position before the pixel's stop (false past the live list and for
+        // lanes without an entry, since every stop index is at most the list length)
+        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
+        if (i >= 0 && jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
+          const float one_m = __fsub_rn(1.f, f.alpha);
+          const float w = f.alpha * T;
+          const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
+          Rr = fmaf(-cd, w, Rr);
+          const float dLda = T * cd - __fdividef(Rr, one_m);
+          T = __fmul_rn(T, one_m);
+          v[6] = fmaf(g.x, w, v[6]);
+          v[7] = fmaf(g.y, w, v[7]);
+          v[8] = fmaf(g.z, w, v[8]);
+          const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
+          const float mt = m * f.t, mdy = m * f.dy;
+          v[0] += mt;
+          v[1] += mdy;
+          v[2] = fmaf(mt, f.t, v[2]);
+          v[3] = fmaf(mt, f.dy, v[3]);
+          v[4] = fmaf(mdy, f.dy, v[4]);
+          v[5] += m;
+        }
+      }
+      __syncwarp();   // this chunk's reads before the next chunk's ring writes
     }
     if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
                 v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
@@ -691,7 +707,7 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
       red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
     }
-    __syncwarp();   // the next bucket rewrites this warp's live-pixel arrays
+    __syncwarp();   // the next bucket rewrites this warp's live list
     uint32_t nxt = 0;
     if (lane == 0) nxt = atomicAdd(&s_next, 1u);
     b = (int)__shfl_sync(0xffffffffu, nxt, 0);
@@ -784,21 +800,7 @@ static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
-  constexpr int NP = TW * TH, NW = kSplatThreads / 32;
-  constexpr size_t smem = (size_t)NP * (sizeof(float4) + sizeof(uint32_t)) + (size_t)2 * NW * (NP + 32) * sizeof(float4);
-  if (smem > 48 * 1024) {
-    // opt in once per device (not a stream operation, so also safe while a graph is captured)
-    static bool done[64] = {};
-    int dev = 0;
-    GS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GS_ERR_UNSUPPORTED;
-    if (!done[dev]) {
-      GS_CUDA_TRY(cudaFuncSetAttribute(raster_bwd_splat_kernel<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-      done[dev] = true;
-    }
-  }
-  raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles, kSplatThreads, smem, s>>>(
+  raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles, kSplatThreads, 0, s>>>(
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
