@@ -4,7 +4,9 @@
 A step is one training view through the whole hot path: gs_project (EWA + SH3
 colour) -> gs_bin_sort -> gs_raster_fwd (Eq. 2) -> gs_l1_loss_grad ->
 gs_raster_bwd -> gs_project_bwd (parameter gradients, with the densification
-statistic fused). Workload: 1.5M Gaussians on 20 surface patches + background,
+statistic fused); by default the raster stages are the per-splat pair
+gs_raster_fwd_ckpt / gs_raster_bwd_splat (--backward pixel: the per-pixel pair,
+same gradients up to summation order). Workload: 1.5M Gaussians on 20 surface patches + background,
 SH degree 3, one 1246x826 view per step on a radius-4 orbit, 16x16 tiles (the
 synthetic stand-in for the paper's MipNeRF-360-scale scenes). Inputs are resident
 in HBM; the 354 MB of parameters the step reads exceed the 129 MB L2.
@@ -14,7 +16,7 @@ pinned host memory, loss read back, every step), the roofline of the dominant
 kernel, per-stage times, the batched mixed-resolution form (12 views in one
 launch per stage, CUDA graph, knobs picked by the autotuner) beside its per-view
 form, the large scene (5M Gaussians, 4 views at 1600x1060) with stored and
-recomputed stop indices and their device memory, and the FP64 oracle timed on the
+recomputed stop indices and with the per-splat backward, and their device memory, and the FP64 oracle timed on the
 host cores on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -64,7 +66,7 @@ def parse():
     ap.add_argument("--cpu-sample-tiles", type=int, default=160)
     ap.add_argument("--n", type=int, default=1_500_000)
     ap.add_argument("--tile", default="16x16", help="tile shape WxH (16x16, 8x8, 16x32, 32x16)")
-    ap.add_argument("--backward", choices=["pixel", "splat"], default="pixel",
+    ap.add_argument("--backward", choices=["pixel", "splat"], default="splat",
                     help="per-pixel gs_raster_bwd or per-splat gs_raster_bwd_splat")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no e2e, batched or CPU legs): for profiler runs")
@@ -309,7 +311,9 @@ def bench_ours(args, rank, local_rank, world):
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "traffic": None}
-    traffic = load_traffic(dom)
+    if dom == "raster_bwd":
+        roof["kernel"] = "raster_bwd_splat" if args.backward == "splat" else "raster_bwd"
+    traffic = load_traffic(roof["kernel"])
     if traffic is not None:
         roof["traffic"] = traffic
 
@@ -320,7 +324,7 @@ def bench_ours(args, rank, local_rank, world):
         "data": "synthetic (seeded surface-patch scene standing in for MipNeRF-360-scale captures)",
         "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "sh_degree": sc.sh_degree,
                    "width": sc.cameras[0].width, "height": sc.cameras[0].height, "tile": args.tile,
-                   "views_per_step": frame.n_views, "duplicates_M": M, "pairs_examined": p_exam,
+                   "backward": args.backward, "views_per_step": frame.n_views, "duplicates_M": M, "pairs_examined": p_exam,
                    "pairs_walked_bwd": p_walk_bwd,
                    "pairs_composited": p_contrib, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (354 MB parameters read per step)"},
@@ -433,7 +437,8 @@ def bench_batched(args, dev):
 def bench_large(args, dev):
     """5M Gaussians, 4 views at 1600x1060 in one launch per stage (graph-replayed),
     with the per-pixel stop index stored by the forward and, as where memory binds,
-    recomputed by the backward; device memory beside views/s for both."""
+    recomputed by the backward, and with the per-splat backward (which also holds
+    the forward's checkpoints); device memory beside views/s for each."""
     import gc
     import torch
     from paper_2507_20239_gb300 import rasterizer as R, synth
@@ -443,14 +448,15 @@ def bench_large(args, dev):
     M = duplicates(P, sc.sh_degree, R.Frame(sc.cameras, device=dev))
     out = {"workload": "large-5M-sh3-4views-1600x1060", "n_gaussians": sc.n, "views_per_launch": len(sc.cameras),
            "duplicates_M": M}
-    for mode, store in (("stop_stored", True), ("stop_recomputed", False)):
+    for mode, store, bwd in (("stop_stored", True, "pixel"), ("stop_recomputed", False, "pixel"),
+                             ("per_splat", True, "splat")):
         gc.collect()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats(dev)
         free0, _ = torch.cuda.mem_get_info(dev)
         base = torch.cuda.memory_allocated(dev)
-        step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(), device=dev,
+        step = TrainStep(P, sc.sh_degree, sc.cameras, sc.targets, StepConfig(backward=bwd), device=dev,
                          capacity=int(M * 1.1) + 4096, store_stop=store)
         g = step.capture(warmup=2)
         for _ in range(2):

@@ -645,6 +645,10 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       if (pn >= 0) kn = ck[pn];
     };
     fetch(lane);
+    // ring slots 32..63 read as stopped until the second chunk replaces them: lanes
+    // whose pixel index is still negative (i & 63 in 33..63) need no bounds test
+    ra[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rb[32 + lane] = make_float4(0.f, 0.f, 1.f, 0.f);
     float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float T = 1.f, Rr = 0.f;
     const uint32_t jj = (uint32_t)j;
@@ -667,18 +671,17 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
       const int s1 = min(s0 + 32, nl + 31);
 #pragma unroll 2
       for (int s = s0; s < s1; ++s) {
-        const int i = s - lane;
-        const int ic = max(i, 0) & (kSplatRing - 1);
+        const int ic = (s - lane) & (kSplatRing - 1);
         const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
         const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
         const float4 q = rb[ic];
         const float4 g = ra[ic];
         T = lane == 0 ? q.z : Tin;
         Rr = lane == 0 ? q.w : Rin;
-        // a list position before the pixel's stop (false past the live list and for
+        // a list position before the pixel's stop (false on stopped slots and for
         // lanes without an entry, since every stop index is at most the list length)
         const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
-        if (i >= 0 && jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
+        if (jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
           const float one_m = __fsub_rn(1.f, f.alpha);
           const float w = f.alpha * T;
           const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
