@@ -112,7 +112,8 @@ __device__ __forceinline__ int warp_select(const float4 *s_rgb, int cnt, int war
 // 8x8 block (the ellipse's x-extent over the block's rows against its columns) and
 // stages it in the warp's shared slots if it passes; the warp then composites the
 // passing entries in list order. A warp leaves as soon as its 64 pixels have
-// stopped, so neither barriers nor finished neighbours hold it.
+// stopped, so neither barriers nor finished neighbours hold it (one-warp CTAs,
+// which also free a finished warp's slot, measured no faster).
 template <int TW, int TH, bool CKPT>
 __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
@@ -123,7 +124,8 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   __shared__ float2 s_xy[NW][32];
   __shared__ float4 s_co[NW][32];
   __shared__ float4 s_rgb[NW][32];
-  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int tile = blockIdx.x;
+  const TileCoord tc = tile_coord(cams, n_views, tile);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   int lx, ly;
   pixel_of<TW>(t, lx, ly);
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   float r0 = 0.f, g0 = 0.f, b0 = 0.f, r1 = 0.f, g1 = 0.f, b1 = 0.f;
   uint32_t st0 = 0, st1 = 0;
   bool done0 = !in0, done1 = !in1;
-  const uint2 rg = ranges[blockIdx.x];
+  const uint2 rg = ranges[tile];
   const int n = (int)(rg.y - rg.x);
   // software pipeline: the record id two steps ahead, the record one step ahead
   uint32_t r_next = lane < n ? vals[rg.x + lane] : 0u;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     if (__all_sync(0xffffffffu, done0 && done1)) break;
     if (CKPT) {
       // state before list position base: (T, accumulated colour) for the per-splat backward
-      float4 *ck = ckpt + (ckpt_bucket(rg.x, blockIdx.x) + (uint64_t)(base >> 5)) * (TW * TH) + ly * TW + lx;
+      float4 *ck = ckpt + (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * (TW * TH) + ly * TW + lx;
       if (!done0) ck[0] = make_float4(T0, r0, g0, b0);
       if (!done1) ck[1] = make_float4(T1, r1, g1, b1);
     }
@@ -544,24 +546,27 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
 
 // Per-splat backward (the per-splat parallel back-propagation of the Taming-3DGS
 // lineage that the paper's base trainer uses): the same gradient as
-// raster_bwd_kernel, parallel over list entries instead of pixels. One CTA per tile;
-// its warps claim the tile's 32-entry buckets (up to the tile's largest stop index)
-// one at a time, one entry per lane. A bucket's live pixels (stop index beyond its
+// raster_bwd_kernel, parallel over list entries instead of pixels. The warps of a
+// tile's CTAs claim its 32-entry buckets (up to the tile's largest stop index) one
+// at a time, one entry per lane. A bucket's live pixels (stop index beyond its
 // first position) start from the forward's checkpoint (T and the colour composited
 // before the bucket) and flow through the warp diagonally: at step s lane l works on
 // live pixel s - l, taking (T, R) from lane l - 1, which handled that pixel one step
-// earlier, in list order. Each lane sums its entry's moments over the tile's pixels
-// in registers and adds them to the record gradients once, with no cross-lane
-// reduction. Since the lanes only ever read 32 consecutive live pixels, a warp keeps
-// them in a 64-slot ring refilled every 32 steps (the next 32 pixels' checkpoints are
-// loaded meanwhile), which keeps shared memory per CTA small and occupancy high.
+// earlier, in list order. A tile's buckets are shared by kSplatSplit CTAs, so a tile
+// with a long list does not hold the end of the launch. Each lane sums its entry's
+// moments over the tile's pixels in registers and adds them to the record gradients
+// once, with no cross-lane reduction. Since the lanes only ever read 32 consecutive
+// live pixels, a warp keeps them in a 64-slot ring refilled every 32 steps (the next
+// 32 pixels' checkpoints are loaded meanwhile), which keeps shared memory per CTA
+// small and occupancy high.
 // Needs the stop indices and the checkpoints written by the forward
 // (gs_raster_fwd_ckpt).
 constexpr int kSplatThreads = 128;
+constexpr int kSplatSplit = 2;     // CTAs per tile (bucket b goes to CTA b % kSplatSplit)
 constexpr int kSplatRing = 64;
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
+__global__ void __launch_bounds__(kSplatThreads, 9) raster_bwd_splat_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
@@ -575,7 +580,8 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
   __shared__ float4 s_ra[NW][kSplatRing];          // ring: (dL/dout, stop bits) of live pixel i at i % 64
   __shared__ float4 s_rb[NW][kSplatRing];          // ring: (x, y, T, R) at the bucket start
   __shared__ uint32_t s_max, s_next;
-  const TileCoord tc = tile_coord(cams, n_views, blockIdx.x);
+  const int tile = blockIdx.x / kSplatSplit, part = blockIdx.x % kSplatSplit;
+  const TileCoord tc = tile_coord(cams, n_views, tile);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (t == 0) {
@@ -606,15 +612,16 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
     if (lane == 0) atomicMax(&s_max, mx);
   }
   __syncthreads();
-  const uint2 rg = ranges[blockIdx.x];
+  const uint2 rg = ranges[tile];
   const int n = min((int)(rg.y - rg.x), (int)s_max);
   const int nb = (n + 31) >> 5;
-  const uint64_t bk0 = ckpt_bucket(rg.x, blockIdx.x);
+  const uint64_t bk0 = ckpt_bucket(rg.x, tile);
   uint16_t *live = s_live[warp];
   float4 *ra = s_ra[warp], *rb = s_rb[warp];
-  // bucket b = warp first, then the next unclaimed one (earlier buckets hold more
-  // live pixels, so a fixed round robin would load the warps unevenly)
-  for (int b = warp; b < nb;) {
+  // this CTA's buckets b = part + kSplatSplit c: c = warp first, then the next
+  // unclaimed one (earlier buckets hold more live pixels, so a fixed round robin
+  // would load the warps unevenly)
+  for (int b = part + kSplatSplit * warp; b < nb;) {
     const int j = 32 * b + lane;   // this lane's list position
     const bool has = j < n;
     uint32_t r = 0;
@@ -713,7 +720,7 @@ __global__ void __launch_bounds__(kSplatThreads) raster_bwd_splat_kernel(
     __syncwarp();   // the next bucket rewrites this warp's live list
     uint32_t nxt = 0;
     if (lane == 0) nxt = atomicAdd(&s_next, 1u);
-    b = (int)__shfl_sync(0xffffffffu, nxt, 0);
+    b = part + kSplatSplit * (int)__shfl_sync(0xffffffffu, nxt, 0);
   }
 }
 
@@ -803,7 +810,7 @@ static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
-  raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles, kSplatThreads, 0, s>>>(
+  raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
