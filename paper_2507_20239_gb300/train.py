@@ -51,6 +51,7 @@ class Schedule:
     sparse_adam: bool = True
     position_lr_final: float = 0.01     # fraction of the initial positional rate reached at the end
     opacity_reset_every: int = 3000
+    backward: str = "pixel"            # raster backward: "pixel" or "splat" (same gradients)
 
     def stage(self, it):
         cur = self.stages[0]
@@ -113,7 +114,7 @@ class Trainer:
         _, r, _ = self.sched.stage(it)
         v = it % len(self.frames[r])
         frame, target = self.frames[r][v], self.targets[r][v]
-        image, _ = rasterize(self.P, self.sh_degree(it), frame, stats=self.stats)
+        image, _ = rasterize(self.P, self.sh_degree(it), frame, stats=self.stats, backward=self.sched.backward)
         if self.sched.ssim_lambda > 0:
             d_image, loss = O.photometric_loss_grad(frame, image.detach(), target, self.sched.ssim_lambda)
         else:
@@ -241,12 +242,14 @@ def main(argv=None):
     ap.add_argument("--energy", type=int, default=0, metavar="K",
                     help="derive the stages from the targets' energy schedule with scales 1..K "
                          "(default: fixed thirds at 1/4, 1/2, full resolution)")
+    ap.add_argument("--backward", choices=["pixel", "splat"], default="pixel",
+                    help="raster backward: per-pixel or per-splat (same gradients)")
     args = ap.parse_args(argv)
     s = args.steps / 3000.0
     sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
                              (int(2000 * s), 1, R.DENSIFY_ADAPTIVE)], total=args.steps,
                      densify_until=int(2500 * s), sh_every=max(1, int(750 * s)),
-                     grad_threshold=args.grad_threshold)
+                     grad_threshold=args.grad_threshold, backward=args.backward)
     gt = synth.surface_scene(13, args.gt, 3)
     energy = None
     if args.energy:
