@@ -45,7 +45,9 @@ class Schedule:
     sh_every: int = 750
     grad_threshold: float = 2e-4
     scale_fraction: float = 0.01       # split when the max scale exceeds this fraction of the extent
-    prune_tau: float = 0.005
+    prune_tau: float = 0.005            # fixed pruning: opacity below this
+    prune_ratio: Optional[float] = None  # adaptive pruning (Sec. "Adaptive Opacity Pruning"): p
+    prune_upper_tau: float = 0.05       # adaptive pruning: tau_u
     seed: int = 3
     ssim_lambda: float = 0.2
     sparse_adam: bool = True
@@ -137,8 +139,13 @@ class Trainer:
         _, r, mode = self.sched.stage(it)
         thr_s = np.float32(math.log(self.sched.scale_fraction * self.extent))
         prune_logit = np.float32(math.log(self.sched.prune_tau / (1.0 - self.sched.prune_tau)))
+        upper_logit = np.float32(math.log(self.sched.prune_upper_tau / (1.0 - self.sched.prune_upper_tau)))
+        if self.sched.prune_ratio is None:
+            prune = dict(prune_logit=prune_logit)
+        else:   # tau = min(k-th smallest logit of the post-densification multiset, logit(tau_u))
+            prune = dict(prune_ratio=self.sched.prune_ratio, prune_upper_logit=upper_logit)
         cfg = R.densify_cfg(mode=mode, grad_threshold=self.sched.grad_threshold, log_scale_threshold=thr_s,
-                            prune_logit=prune_logit, seed=self.sched.seed, event=self.event)
+                            seed=self.sched.seed, event=self.event, **prune)
         P = {k: self.P[k].detach() for k in PARAM_KEYS}
         split, clone, tau, new_n, ws = R.densify_select(cfg, P, self.stats.accum, self.stats.count)
         extra = {k: v.contiguous() for k, v in self.opt.moments().items()}
@@ -150,6 +157,7 @@ class Trainer:
             raise RuntimeError("densify: output capacity")
         if self.on_densify is not None:
             self.on_densify(dict(it=it, mode=mode, cfg=cfg, thr_s=thr_s, prune_logit=prune_logit,
+                                 prune_ratio=self.sched.prune_ratio, prune_upper_tau=self.sched.prune_upper_tau,
                                  params=P, accum=self.stats.accum, count=self.stats.count, extra=extra,
                                  split=split, clone=clone, tau=tau, out=out, out_extra=ex, seed=self.sched.seed,
                                  event=self.event))
@@ -244,12 +252,17 @@ def main(argv=None):
                          "(default: fixed thirds at 1/4, 1/2, full resolution)")
     ap.add_argument("--backward", choices=["pixel", "splat"], default="pixel",
                     help="raster backward: per-pixel or per-splat (same gradients)")
+    ap.add_argument("--prune-ratio", type=float, default=None, metavar="P",
+                    help="adaptive opacity pruning with ratio P (default: fixed tau 0.005)")
+    ap.add_argument("--prune-upper", type=float, default=0.05, metavar="TAU_U",
+                    help="adaptive pruning's upper bound on tau")
     args = ap.parse_args(argv)
     s = args.steps / 3000.0
     sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
                              (int(2000 * s), 1, R.DENSIFY_ADAPTIVE)], total=args.steps,
                      densify_until=int(2500 * s), sh_every=max(1, int(750 * s)),
-                     grad_threshold=args.grad_threshold, backward=args.backward)
+                     grad_threshold=args.grad_threshold, backward=args.backward,
+                     prune_ratio=args.prune_ratio, prune_upper_tau=args.prune_upper)
     gt = synth.surface_scene(13, args.gt, 3)
     energy = None
     if args.energy:
@@ -268,7 +281,8 @@ def main(argv=None):
     n_clone = sum(e[3] for e in tr.events)
     print(json.dumps({"history": hist, "final_n": tr.n, "events": tr.events,
                       "new_from_clone": n_clone / max(1, n_clone + 2 * n_split), "init_log_scale": args.init_log_scale,
-                      "grad_threshold": args.grad_threshold, "energy_schedule": energy}))
+                      "grad_threshold": args.grad_threshold, "prune_ratio": args.prune_ratio,
+                      "prune_upper": args.prune_upper, "energy_schedule": energy}))
 
 
 if __name__ == "__main__":

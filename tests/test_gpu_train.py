@@ -3,7 +3,8 @@ at 1/4 and 1/2 resolution, clone re-enabled at full resolution, prune below
 opacity 0.005, SH degree rising) trained on the library's kernels, with every
 densification event checked against the oracle on the same FP32 tensors: split and
 clone masks, the prune threshold and the whole compaction (parameters and the Adam
-moments carried through it) bit-exact, split children's means within 1e-5."""
+moments carried through it) bit-exact, split children's means within 1e-5; once
+with fixed and once with adaptive opacity pruning."""
 import math
 
 import numpy as np
@@ -18,9 +19,8 @@ from paper_2507_20239_gb300.train import Schedule, Trainer, orbit_views, render_
 pytestmark = pytest.mark.gpu
 
 
-def test_global_to_local_training_with_checked_densification():
-    events = []
-
+def _checker(events, adaptive):
+    """on_densify callback: the event recomputed by the oracle on the same FP32 tensors."""
     def check(ev):
         np_ = lambda t: t.detach().cpu().numpy()
         p = {k: np_(v) for k, v in ev["params"].items()}
@@ -28,7 +28,11 @@ def test_global_to_local_training_with_checked_densification():
         ws_, wc = oden.select(accum, count, p["log_scales"], ev["mode"], np.float32(2e-4), ev["thr_s"])
         assert np.array_equal(np_(ev["split"]).astype(bool), ws_)
         assert np.array_equal(np_(ev["clone"]).astype(bool), wc)
-        tau = oden.prune_threshold(p["opacity_logits"], ws_, wc, fixed_tau=0.005)
+        if adaptive:
+            assert ev["prune_ratio"] == 0.03 and ev["prune_upper_tau"] == 0.05
+            tau = oden.prune_threshold(p["opacity_logits"], ws_, wc, p=0.03, tau_u=0.05)
+        else:
+            tau = oden.prune_threshold(p["opacity_logits"], ws_, wc, fixed_tau=0.005)
         assert np.float32(ev["tau"].item()) == tau
         extra = {k: np_(v) for k, v in ev["extra"].items()}
         want, wex, idx = oden.apply(p, ws_, wc, tau, ev["seed"], ev["event"], extra=extra)
@@ -42,7 +46,15 @@ def test_global_to_local_training_with_checked_densification():
         assert np.array_equal(out["means"][:base], want["means"][:base].astype(np.float32))
         if base < out["means"].shape[0]:
             assert np.abs(out["means"][base:] - want["means"][base:]).max() < 1e-5
-        events.append((ev["it"], ev["mode"], int(ws_.sum()), int(wc.sum()), len(idx["source"])))
+        n_pruned = len(p["means"]) + int(wc.sum()) + int(ws_.sum()) - len(idx["source"])
+        events.append((ev["it"], ev["mode"], int(ws_.sum()), int(wc.sum()), len(idx["source"]), n_pruned,
+                       float(tau)))
+    return check
+
+
+def test_global_to_local_training_with_checked_densification():
+    events = []
+    check = _checker(events, adaptive=False)
 
     cams = orbit_views(4, 623, 413, 623.0)
     gt = synth.surface_scene(13, 200_000, 3)
@@ -58,3 +70,25 @@ def test_global_to_local_training_with_checked_densification():
     assert sum(e[2] for e in events) > 0 and sum(e[3] for e in events[3:]) > 0
     assert tr.n > 20_000
     assert hist[-1][2] < hist[0][2]                                # the L1 loss went down
+
+
+def test_adaptive_opacity_pruning_in_training():
+    """The same schedule with adaptive pruning (p = 0.03, tau_u = 0.05): every event's
+    threshold is the k-th smallest logit of the post-densification multiset, capped
+    at logit(tau_u), and the whole event is bit-exact against the oracle."""
+    events = []
+    cams = orbit_views(4, 312, 207, 312.0)
+    gt = synth.surface_scene(13, 60_000, 3)
+    views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
+    init = synth.surface_scene(3, 10_000, 3).params()
+    sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (200, 2, R.DENSIFY_SPLIT_ONLY),
+                             (400, 1, R.DENSIFY_ADAPTIVE)], total=600, densify_until=500, sh_every=150,
+                     prune_ratio=0.03, prune_upper_tau=0.05)
+    tr = Trainer(init, views, sched, extent=1.1 * 4.0, on_densify=_checker(events, adaptive=True))
+    hist = tr.run(log_every=100)
+    assert [e[0] for e in events] == [100, 200, 300, 400, 500]
+    # adaptive pruning removes at most 3% of the post-densification set at an event
+    # (fewer when the cap logit(tau_u) binds)
+    assert sum(e[5] for e in events) > 0
+    assert all(e[5] <= math.floor(0.03 * (e[4] + e[5])) for e in events)
+    assert hist[-1][2] < hist[0][2]
