@@ -112,3 +112,36 @@ def test_host_argument_checks_return_invalid_arg(lib):
     p = _abi.GsParams()
     p.n, p.sh_degree, p.sh_stride = 10, 4, 25       # degree 4 is not supported
     assert lib.gs_project(C.byref(p), C.byref(fr), None, None) == 1
+
+
+def test_checkpoint_size_and_bucket_layout(lib):
+    """gs_raster_ckpt_size's formula, and the bucket numbering it relies on: tile t's
+    32-entry buckets b are floor(s_t / 32) + t + b for a list starting at s_t, which
+    never overlap between tiles and stay below ceil(M / 32) + n_tiles."""
+    import numpy as np
+    cams = (_abi.GsCamera * 2)()
+    for i, (w, h) in enumerate([(623, 413), (1246, 826)]):
+        cams[i].width, cams[i].height = w, h
+        cams[i].fx = cams[i].fy = 100.0
+        cams[i].near_plane = 0.2
+    for tw, th in ((16, 16), (8, 8), (16, 32)):
+        fr = _abi.GsFrame()
+        assert lib.gs_frame_init(cams, 2, tw, th, C.byref(fr)) == 0
+        for cap in (0, 1, 31, 32, 33, 1_000_003):
+            assert lib.gs_raster_ckpt_size(C.byref(fr), cap) == ((cap + 31) // 32 + fr.n_tiles) * tw * th * 16
+        assert lib.gs_raster_ckpt_size(C.byref(fr), -1) == 0
+    assert lib.gs_raster_ckpt_size(None, 10) == 0
+    assert lib.gs_raster_fwd_ckpt(None, None, None, None, None, None, None, None, 0, None) == 1
+    assert lib.gs_raster_bwd_splat(None, None, None, None, None, None, None, 0, None, None) == 1
+    rng = np.random.default_rng(0)
+    for trial in range(200):
+        n_tiles = int(rng.integers(1, 60))
+        lens = rng.choice([0, 1, 31, 32, 33, 64, 100], n_tiles) * (rng.random(n_tiles) < 0.8)
+        starts = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        M = int(lens.sum())
+        used = set()
+        for t in range(n_tiles):
+            for b in range((int(lens[t]) + 31) // 32):
+                k = int(starts[t]) // 32 + t + b
+                assert k not in used and k < (M + 31) // 32 + n_tiles, (trial, t, b)
+                used.add(k)
