@@ -359,16 +359,29 @@ def tile_sync_stats(frame, counts):
     return {"needed": need, "walked_tile": walked, "walked_warp": walked_w}
 
 
+def rasterizer_code_hash():
+    """sha256 of the rasterizer's code (raster.cu and gs_common.cuh without // comments,
+    trailing blanks and empty lines): what the recorded DRAM counters were taken on."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2507_20239_gb300", "csrc")
+    lines = []
+    for name in ("raster.cu", "gs_common.cuh"):
+        with open(os.path.join(csrc, name)) as f:
+            for line in f:
+                code = re.sub(r"//.*$", "", line.rstrip("\n")).rstrip()
+                if code:
+                    lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def load_traffic(kernel):
     """Per-launch DRAM bytes of a kernel from the committed ncu summary, used only
-    while the rasterizer sources are the ones the counters were taken on."""
-    import hashlib
+    while the rasterizer code is the one the counters were taken on."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        csrc = os.path.join(ROOT, "paper_2507_20239_gb300", "csrc")
-        src = b"".join(open(os.path.join(csrc, n), "rb").read() for n in ("raster.cu", "gs_common.cuh"))
-        if hashlib.sha256(src).hexdigest() != t.get("source_sha256"):
+        if rasterizer_code_hash() != t.get("code_sha256"):
             return None
         return t.get(kernel)
     except Exception:

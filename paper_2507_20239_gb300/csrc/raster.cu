@@ -1,22 +1,24 @@
 // Front-to-back alpha compositing (the paper's Eq. 2) and its gradient.
 //
-// One CTA per tile, two horizontally adjacent pixels per thread; each warp owns an
-// 8x8 block of the tile. The tile's depth-ordered list is consumed in batches of one
-// record per thread, staged in shared memory together with a mask of the 8x8
-// blocks the record's footprint ellipse reaches (per 8-row band, the ellipse's
-// x-extent against the blocks' columns), so a warp skips the records that cannot
-// touch its pixels. A pixel stops before the
-// entry that would drive its transmittance below 1e-4 and the CTA leaves once every
-// pixel has stopped.
+// Forward: one CTA per tile, two horizontally adjacent pixels per thread; each warp
+// owns an 8x8 block of the tile and walks the tile's depth-ordered list on its own,
+// 32 entries at a time, keeping only the entries whose footprint ellipse (where
+// alpha can reach the 1/255 floor) meets its block. A pixel stops before the entry
+// that would drive its transmittance below 1e-4; a warp leaves once its 64 pixels
+// have stopped. Optionally it stores each pixel's stop index and, for the per-splat
+// backward, a checkpoint (T, composited colour) every 32 list entries.
 //
-// The backward pass re-walks the list front to back with exactly the forward's
-// FP32 decisions (no stored stop index) and needs, per pixel, only <dL/dout, out>:
+// Both backward kernels re-walk the lists front to back with exactly the forward's
+// FP32 decisions and need, per pixel, only <dL/dout, out>:
 //   dL/dsigma_i = T_i <c_i, g> - (<out, g> - sum_{j<=i} <c_j, g> sigma_j T_j) / (1 - sigma_i).
-// The 9 per-(pixel, Gaussian) terms (six moments of the falloff gradient, three
-// colour terms) are summed over the thread's two
-// pixels in registers, across the warp with a transposing shuffle reduction, across
-// the CTA's warps in shared memory, and then added once per (tile, record) to the
-// record gradients with vector reductions.
+// Per (pixel, Gaussian) they accumulate six moments of the falloff gradient and
+// three colour terms, turned into the record gradients once per (tile, record).
+// raster_bwd_kernel is parallel over pixels: the terms are summed over a thread's
+// two pixels in registers, across the warp with a transposing shuffle reduction and
+// across the CTA's warps in shared memory, then added with vector reductions.
+// raster_bwd_splat_kernel is parallel over list entries (one lane per entry, the
+// pixels flowing through the warp from the forward's checkpoints), so each lane
+// sums its own entry's terms and no reduction is needed.
 #include "gs_common.cuh"
 
 namespace gs {
