@@ -48,3 +48,54 @@ def test_large_view_raster_recomputed_stop_sampled_tiles(large):
     for k in got:
         e = rel_l2(got[k], g[k])
         assert e < GRAD_TOL, (k, e)
+
+
+def test_large_views_per_splat_backward(large):
+    """The per-splat backward at the large scene's size: view 0 on sampled tiles
+    against the FP64 oracle, and the four views in one training step (the
+    benchmark's launch configuration) against the per-pixel step: identical images,
+    gradients within summation order."""
+    from paper_2507_20239_gb300.step import StepConfig, TrainStep, duplicates
+    from tests.gs_fixtures import records_to_gpu
+    cam = large.cameras[0]
+    tile = (16, 16)
+    rec = oracle_records_fp32(large.params(), large.sh_degree, cam, tile)
+    frame = R.Frame([cam], tile=tile)
+    proj = records_to_gpu([rec])
+    bins = R.bin_sort(proj, frame)
+    ckpt = R.alloc_ckpt(frame, bins)
+    img, T, stop = R.raster_fwd_ckpt(proj, bins, frame, ckpt)
+    ranges = bins.ranges.cpu().numpy()
+    lens = ranges[:, 1] - ranges[:, 0]
+    rng = np.random.default_rng(42)
+    busy = np.nonzero(lens > 0)[0]
+    tiles = sorted(set(rng.choice(busy, 16, replace=False).tolist()) | set(np.argsort(lens)[-2:].tolist()))
+    mask = _tile_mask(cam, tile, tiles)
+    d_image = np.where(mask[None], rng.normal(0, 1, (3, cam.height, cam.width)), 0).astype(np.float32)
+    _, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
+    rs = R.raster_bwd_splat(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda(), stop, ckpt)
+    torch.cuda.synchronize()
+    got = dict(d_mean2d=rs.d_mean2d.cpu().numpy(), d_conic=rs.d_conic_opacity[:, :3].cpu().numpy(),
+               d_opacity=rs.d_conic_opacity[:, 3].cpu().numpy(), d_rgb=rs.d_rgb[:, :3].cpu().numpy())
+    for k in got:
+        e = rel_l2(got[k], g[k])
+        assert e < GRAD_TOL, (k, e)
+    del proj, bins, ckpt, img, T, stop, rs
+
+    P = R.to_device_params(large.params(), "cuda")
+    M = duplicates(P, large.sh_degree, R.Frame(large.cameras))
+    out = {}
+    for bw in ("pixel", "splat"):
+        st = TrainStep(P, large.sh_degree, large.cameras, large.targets, StepConfig(backward=bw),
+                       capacity=int(M * 1.1) + 4096)
+        st.run()
+        torch.cuda.synchronize()
+        assert st.error() == 0
+        out[bw] = (st.image.clone(), st.loss.clone(), {k: v.clone() for k, v in st.pgrads.items()})
+        del st
+        torch.cuda.empty_cache()
+    assert torch.equal(out["pixel"][0], out["splat"][0])
+    assert torch.allclose(out["pixel"][1], out["splat"][1], rtol=1e-5, atol=0)   # atomic partial sums
+    for k in R.PARAM_KEYS:
+        e = rel_l2(out["splat"][2][k].cpu().numpy(), out["pixel"][2][k].cpu().numpy())
+        assert e < 1e-4, (k, e)
