@@ -418,15 +418,24 @@ __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
     const int64_t g0 = base + wib * 32;
     const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
     if (STAGED) {
+      // rows of Gaussians culled in every view are not read: their coefficients are
+      // never used and their gradient rows are zero
+      bool seen = false;
+      if (g < n)
+        for (int v = 0; v < n_views && !seen; ++v) seen = proj.radius[(int64_t)v * n + g] > 0;
+      const uint32_t vmask = __ballot_sync(0xffffffffu, seen);
       const float *src = P.sh + g0 * RW;
       if (RW % 4 == 0 && vec) {   // rows of 3K floats, K = 4 or 16: whole float4s, none across rows
         for (int f4 = lane; f4 < rows * RW / 4; f4 += 32) {
+          const int row = (4 * f4) / RW;
+          if (!((vmask >> row) & 1u)) continue;
           const float4 x = reinterpret_cast<const float4 *>(src)[f4];
-          float *d = wsh + ((4 * f4) / RW) * RP + (4 * f4) % RW;
+          float *d = wsh + row * RP + (4 * f4) % RW;
           d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
         }
       } else {
-        for (int f = lane; f < rows * RW; f += 32) wsh[(f / RW) * RP + (f % RW)] = src[f];
+        for (int f = lane; f < rows * RW; f += 32)
+          if ((vmask >> (f / RW)) & 1u) wsh[(f / RW) * RP + (f % RW)] = src[f];
       }
       __syncwarp();
     }
