@@ -326,6 +326,9 @@ gs_status_t gs_densify_select(const gs_densify_cfg_t *cfg, const float *log_scal
  *  - The first call on a device looks up the array's device address on the current
  *    device (cudaGetSymbolAddress) and caches it; make that first call before any
  *    stream capture on the device.
+ *  - The cached address is not valid across cudaDeviceReset: after a reset of a
+ *    device in the same process the next call would use a stale device address.
+ *    Do not reset a device between calls to this entry point.
  *  - Every call shares the one array and clears it on its stream before use; calls
  *    that overlap on the GPU (different streams, or concurrent threads) race on it.
  *  - Calls no cudaMalloc, cudaFree or allocating routine. */

@@ -5,7 +5,7 @@ densification bookkeeping compute, written from the paper (Sec. "Preliminary":
 Eq. 1 Gaussian, the EWA projection Sigma' = J W Sigma W^T J^T, Eq. 2 front-to-back
 alpha compositing; the densification rule; Sec. "Adaptive Opacity Pruning").
 Where the paper is silent, the reading taken is the one listed in the design notes
-(near plane 0.2, 0.3 px^2 low-pass dilation, 3-sigma extent, 1/255 alpha floor,
+(near plane 0.2, 0.3 px^2 low-pass dilation, the 1/255-floor footprint, 1/255 alpha floor,
 alpha clamp 0.99, transmittance cutoff 1e-4, ...); each function states it.
 
 Rules this package obeys:

@@ -44,11 +44,13 @@ def proj_record_arrays(proj: dict) -> dict:
 
 
 def render_view(params: dict, sh_degree: int, cam, target=None, tile_w=16, tile_h=16,
-                bg=(0.0, 0.0, 0.0), tiles=None, d_image=None):
+                bg=(0.0, 0.0, 0.0), tiles=None, d_image=None, rec_delta=None):
     """Forward (and, given a target or d_image, backward) of one view.
 
     Returns a dict with the projection (numpy), the render outputs, the loss and
     d_image when a target is given, record gradients and parameter gradients.
+    rec_delta [N,6]: differences of the records another implementation computed
+    (see raster.composite; they widen the straddle flags).
     """
     p = params_to_torch(params)
     with torch.no_grad():
@@ -60,17 +62,18 @@ def render_view(params: dict, sh_degree: int, cam, target=None, tile_w=16, tile_
     if target is None and d_image is None:
         rec = records_to_torch(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"])
         with torch.no_grad():
-            res["render"] = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles)
+            res["render"] = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles,
+                                      rec_delta=rec_delta)
         return res
     if d_image is None:
         with torch.no_grad():
             rec = records_to_torch(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"])
-            fwd = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles)
+            fwd = rasterize(rec, lists, cam.width, cam.height, tile_w, tile_h, bg, tiles, rec_delta=rec_delta)
         loss, d_image = l1_loss_grad(fwd["image"], target)
         res["loss"] = loss
     res["d_image"] = d_image
     out, g = raster_vjp(proj["mean2d"], proj["conic_f"], proj["opacity"], proj["rgb"], lists,
-                        cam.width, cam.height, d_image, tile_w, tile_h, bg, tiles)
+                        cam.width, cam.height, d_image, tile_w, tile_h, bg, tiles, rec_delta)
     res["render"] = out
     res["rec_grads"] = g
     res["param_grads"] = project_vjp(params, sh_degree, [cam], [g], tile_w, tile_h)

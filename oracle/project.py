@@ -95,37 +95,52 @@ def footprint_half(conic_f: np.ndarray, q_max: np.ndarray) -> np.ndarray:
     return np.stack([np.sqrt(qb * (1.0 / A + b * b / g)), np.sqrt(qb / g)], 1)
 
 
-def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
-    """True where the ellipse A (dx + beta dy)^2 + gamma dy^2 <= qb, d = mean - p,
-    meets the box of pixel centres p in [X0, X1] x [Y0, Y1].
+def box_min_q(u, v, conic, X0, X1, Y0, Y1):
+    """Minimum over the box [X0, X1] x [Y0, Y1] of the screen-space quadratic form of
+    Eq. 1, q(p) = d^T Sigma''^-1 d with d = mean - p, in FP64.
 
-    Elementwise over arrays of one dtype; every operation is a single rounded
-    operation of that dtype (the decision is taken in the precision of the data).
-    If the unconstrained minimum d = 0 lies in the box the test passes; otherwise
-    the minimum of the convex quadratic lies on an edge, at the clamped 1-D
-    minimiser (dx* = -beta dy on a fixed-dy edge, dy* = -(A beta dx) / (A beta^2 + gamma)
-    on a fixed-dx edge, evaluated as -((A beta) dx) (1 / (A beta^2 + gamma)) with the
-    reciprocal formed once per record).
+    conic = (a, b, c), the entries of Sigma''^-1 = [[a, b], [b, c]] (positive
+    definite), so q = a dx^2 + 2 b dx dy + c dy^2. Plain convex geometry: if the mean
+    lies in the box the minimum is 0; otherwise it lies on the box's boundary, and on
+    each edge q is a 1-D quadratic whose unconstrained minimiser (dx = -b dy / a on
+    a horizontal edge, dy = -b dx / c on a vertical one) is clamped to the edge.
+    Every input is promoted to float64; arrays broadcast elementwise.
     """
-    dxl, dxh = u - X1, u - X0
-    dyl, dyh = v - Y1, v - Y0
-    inside = (dxl <= 0) & (dxh >= 0) & (dyl <= 0) & (dyh >= 0)
+    f = lambda x: np.asarray(x, np.float64)
+    u, v, X0, X1, Y0, Y1 = map(f, (u, v, X0, X1, Y0, Y1))
+    a, b, c = (f(x) for x in conic)
+    # d = mean - p ranges over [u - X1, u - X0] x [v - Y1, v - Y0]
+    dx_lo, dx_hi = u - X1, u - X0
+    dy_lo, dy_hi = v - Y1, v - Y0
 
     def q(dx, dy):
-        t = dx + beta * dy
-        return A * (t * t) + gamma * (dy * dy)
+        return a * dx * dx + 2.0 * b * dx * dy + c * dy * dy
 
-    ab = A * beta
-    inv_den = (ab * beta + gamma).dtype.type(1) / (ab * beta + gamma)
-    m = None
-    for f in (dyl, dyh):
-        dx = np.minimum(np.maximum(-(beta * f), dxl), dxh)
-        c = q(dx, f)
-        m = c if m is None else np.minimum(m, c)
-    for e in (dxl, dxh):
-        dy = np.minimum(np.maximum(-((ab * e) * inv_den), dyl), dyh)
-        m = np.minimum(m, q(e, dy))
-    return inside | (m <= qb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        best = np.full(np.broadcast(u, a, X0, Y0).shape, np.inf)
+        for dy in (dy_lo, dy_hi):                     # horizontal edges
+            dx = np.clip(-b * dy / a, dx_lo, dx_hi)
+            best = np.minimum(best, q(dx, dy))
+        for dx in (dx_lo, dx_hi):                     # vertical edges
+            dy = np.clip(-b * dx / c, dy_lo, dy_hi)
+            best = np.minimum(best, q(dx, dy))
+    inside = (dx_lo <= 0) & (dx_hi >= 0) & (dy_lo <= 0) & (dy_hi >= 0)
+    return np.where(inside, 0.0, best)
+
+
+def expand_conic(A, beta, gamma):
+    """(a, b, c) of Sigma''^-1 from the factored record conic (A, beta, gamma), FP64:
+    A (dx + beta dy)^2 + gamma dy^2 = A dx^2 + 2 A beta dx dy + (gamma + A beta^2) dy^2."""
+    A, beta, gamma = (np.asarray(x, np.float64) for x in (A, beta, gamma))
+    return A, A * beta, gamma + A * beta * beta
+
+
+def tile_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
+    """True where the footprint ellipse q <= qb (the region where alpha can reach the
+    1/255 floor, R9) meets the box of pixel centres [X0, X1] x [Y0, Y1]: the box
+    minimum of q (box_min_q) against qb, in FP64. This is the reference test; the
+    binning's FP32 decision procedure is band_span / band_hit below."""
+    return box_min_q(u, v, expand_conic(A, beta, gamma), X0, X1, Y0, Y1) <= np.asarray(qb, np.float64)
 
 
 def band_span(u, v, A, beta, gamma, qb, Y0, Y1):
@@ -140,9 +155,12 @@ def band_span(u, v, A, beta, gamma, qb, Y0, Y1):
     at the extreme clamped into [v - Y1, v - Y0]. A box [X0, X1] x [Y0, Y1] meets the
     ellipse exactly when ok and X1 >= xl and X0 <= xr and xl <= xr (band_hit).
 
-    Elementwise in the inputs' dtype, one rounded operation each (the CUDA binning
-    evaluates the same sequence, with dy_r and 1/A formed once per record);
-    fmax/fmin ignore a NaN operand like C's.
+    This is the decision procedure R9 fixes for the binning: evaluated in FP32 with
+    one rounded operation each (dy_r and 1/A formed once per record; fmax/fmin
+    ignore a NaN operand like C's), it defines the FP32 tile lists whose keys must
+    match bit-exactly. Whether those lists are right is checked against the exact
+    geometry instead: in FP64 it agrees with tile_hit, and in FP32 it stays within
+    band_margin of it (both pinned in the tests).
     Returns (ok, xl, xr); ok is False where the band misses the ellipse.
     """
     dt = np.result_type(u, A)
@@ -167,6 +185,42 @@ def band_hit(u, v, A, beta, gamma, qb, X0, X1, Y0, Y1):
     with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
         ok, xl, xr = band_span(u, v, A, beta, gamma, qb, Y0, Y1)
         return ok & (xl <= xr) & (X1 >= xl) & (X0 <= xr)
+
+
+U32 = 2.0 ** -24      # unit round-off of FP32 round-to-nearest
+
+
+def band_margin(u, v, beta, half_x, half_y, width, height):
+    """How far the FP32 binning decision (band_span in FP32 over the FP32 tile
+    rectangle) can sit from the exact test tile_hit, as a perturbation of the
+    problem: (delta [px], eps [relative]) such that the FP32 decision for a box is
+    the exact decision for some box within delta of it on every side and some bound
+    within qb (1 +- eps).
+
+    Derivation (u_r = 2^-24; inputs u, v, A, beta, gamma, q_max exact FP32 values,
+    box edges exact; first order in u_r):
+      * the band offsets dy = v - Y are rounded once: |error| <= u_r (|v| + H), the
+        same as moving the band's rows;
+      * dy_r only selects where the concave right end (convex left end) is read:
+        its error changes xr, xl to second order;
+      * w = qb - gamma dy^2: |error| <= 3 u_r qb (two products and a difference,
+        gamma dy^2 <= qb where w >= 0); sqrt(w / A) with 1/A, the product and the
+        root each rounded adds 3 u_r relatively to w/A, i.e. 6 u_r qb in w: together
+        an ellipse bound within 9 u_r qb of qb, plus qb = fl(q_max * 1.002f) itself
+        (u_r and the constant's own rounding, < 3e-8);
+      * xr = (u + beta dy) + s: three roundings, |error| <= u_r (3 |u| +
+        3 |beta| (|v| + H) + 2 s) with s <= half_x, the same as moving the box's
+        columns;
+      * the tile rectangle from the FP32 half-extents: |error| <= u_r (|u| + 2 half_x)
+        per column edge and u_r (|v| + 2 half_y) per row edge, again a move of the
+        box's sides.
+    The returned pair is that bound times a safety factor of 4 (second-order terms).
+    """
+    f = lambda x: np.abs(np.asarray(x, np.float64))
+    u, v, beta, hx, hy = f(u), f(v), f(beta), f(half_x), f(half_y)
+    delta = 4.0 * U32 * (4.0 * u + 3.0 * beta * (v + height) + 4.0 * (hx + hy) + 2.0 * v + height + width)
+    eps = 4.0 * (9.0 * U32 + U32) + 3e-8
+    return delta, eps
 
 
 def camera_tensors(cam):

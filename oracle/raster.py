@@ -116,7 +116,43 @@ def tile_lists(rec_arrays: dict, width, height, tile_w=16, tile_h=16):
 # ----------------------------------------------------------------------------------------
 # compositing (FP64, differentiable)
 # ----------------------------------------------------------------------------------------
-def composite(px, py, xy, conic_f, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_tol_T=1e-3):
+U32 = 2.0 ** -24                      # unit round-off of FP32 round-to-nearest
+K_EXP = 0.5 / np.log(2.0)             # |k| = log2(e) / 2: G = 2^(k q), k = -log2(e) / 2
+EX2_REL = 2.0 ** -22                  # ex2.approx.f32: 2 ulp of the result (PTX ISA bound)
+ALPHA_MAX_F32_REL = abs(float(np.float32(ALPHA_MAX)) - ALPHA_MAX) / ALPHA_MAX
+ALPHA_MIN_F32_REL = abs(float(np.float32(ALPHA_MIN)) - ALPHA_MIN) / ALPHA_MIN
+T_MIN_F32_REL = abs(float(np.float32(T_MIN)) - T_MIN) / T_MIN
+FLAG_SAFETY = 2.0                     # first-order bounds below, doubled
+
+
+def fp32_alpha_error(dx, dy, A, beta, gamma, q, rec_dq=None, rec_do=None):
+    """Bound on the relative error of an FP32 evaluation of sigma = o G (Eq. 2),
+    G = exp(-q/2), q = A (dx + beta dy)^2 + gamma dy^2, from exact FP32 record values,
+    with one rounding per operation (u_r = 2^-24, first order):
+      dx = u - p_x, dy = v - p_y      |err| <= u_r |dx|, u_r |dy|
+      t = beta dy + dx (fused)        |err| <= u_r (|t| + |beta dy| + |dx|)
+      k A, k gamma (k = -log2(e)/2)   relative 2 u_r each (k and the product rounded)
+      e = (kA t) t + k gamma (dy dy)  |err| <= |k| u_r (3 A t^2 + 2 A |t| (|t| + |beta dy|
+                                       + |dx|) + 6 gamma dy^2 + q)
+      G = 2^e                         relative ln 2 |err e| + 2^-22 (ex2.approx)
+      o G                             relative + u_r; the 0.99 clamp's FP32 constant
+                                      differs from 0.99 by 1e-8 relatively.
+    rec_dq, rec_do (optional): first-order changes of q and absolute changes of o from
+    perturbed record values (when the two sides project independently).
+    Returns the bound as an array of dx's shape.
+    """
+    at = np.abs(dx + beta * dy)
+    de = K_EXP * U32 * (3 * A * at * at + 2 * A * at * (at + np.abs(beta * dy) + np.abs(dx))
+                        + 6 * gamma * dy * dy + q)
+    eps = np.log(2.0) * de + EX2_REL + U32 + ALPHA_MAX_F32_REL
+    if rec_dq is not None:
+        eps = eps + 0.5 * rec_dq
+    if rec_do is not None:
+        eps = eps + rec_do
+    return eps
+
+
+def composite(px, py, xy, conic_f, opacity, rgb, bg, rec_delta=None):
     """Eq. 2 for P pixels over one depth-ordered list of L Gaussians.
 
     px, py: [P] float64 sample coordinates; xy [L,2], conic_f [L,3] = (A, beta,
@@ -124,8 +160,18 @@ def composite(px, py, xy, conic_f, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_t
     rgb [L,3] torch float64 in list order; bg [3]. Returns (color [P,3], T_final [P],
     stop [P], n_examined [P], n_contrib [P], flag [P]); stop is one past the last
     contributing list position, n_examined counts list entries looked at up to and
-    including the one that triggers the cut-off, flag marks pixels where a
-    cut-off decision lies within the relative tolerances of its threshold.
+    including the one that triggers the cut-off.
+
+    flag marks pixels where an FP32 evaluation of the same walk may take a different
+    decision: an examined entry whose sigma lies within the FP32 error bound of
+    sigma (fp32_alpha_error, times FLAG_SAFETY) of the 1/255 floor, or whose
+    transmittance after it lies within the bound of the running FP32 product of
+    1e-4. The product's bound after composited entries j <= k is
+    rho_k = sum_j (sigma_j eps_j / (1 - sigma_j) + 2 u_r): 1 - sigma_j carries
+    sigma_j's error, and 1 - sigma and T (1 - sigma) are rounded once each.
+    rec_delta (optional, [L,6] absolute differences of (u, v, A, beta, gamma, o)
+    between the records the two sides use) widens the bound by their first-order
+    effect on q and o.
     """
     P = px.shape[0]
     L = xy.shape[0]
@@ -163,13 +209,30 @@ def composite(px, py, xy, conic_f, opacity, rgb, bg, flag_tol_alpha=5e-6, flag_t
     first_np = first.numpy()
     n_exam = np.minimum(first_np + 1, L).astype(np.int64)
     n_contrib = act.sum(1).astype(np.int64)
-    # straddle flags on examined entries
+    # straddle flags on examined entries, from the derived FP32 error bounds
     exam = idx.numpy() < n_exam[:, None]
     a_np = alpha.detach().numpy()
     p_np = power.detach().numpy()
-    fa = exam & (p_np <= 0) & (np.abs(a_np / ALPHA_MIN - 1.0) < flag_tol_alpha)
+    dxn, dyn = dx.detach().numpy(), dy.detach().numpy()
+    cf = conic_f.detach().numpy()
+    An, bn, gn = cf[None, :, 0], cf[None, :, 1], cf[None, :, 2]
+    q = -2.0 * p_np
+    rec_dq = rec_do = None
+    if rec_delta is not None:
+        d = np.asarray(rec_delta, np.float64)[None]            # [1,L,6]
+        tt = dxn + bn * dyn
+        rec_dq = (np.abs(2 * An * tt) * d[..., 0] + np.abs(2 * An * tt * bn + 2 * gn * dyn) * d[..., 1]
+                  + tt * tt * d[..., 2] + np.abs(2 * An * tt * dyn) * d[..., 3] + dyn * dyn * d[..., 4])
+        op = opacity.detach().numpy()[None]
+        rec_do = d[..., 5] / np.maximum(op, 1e-30)
+    eps_a = fp32_alpha_error(dxn, dyn, An, bn, gn, q, rec_dq, rec_do)
+    a_raw = opacity.detach().numpy()[None] * np.exp(p_np)     # sigma before the 0.99 clamp
+    fa = exam & (p_np <= 0) & (np.abs(a_raw / ALPHA_MIN - 1.0) < FLAG_SAFETY * eps_a + ALPHA_MIN_F32_REL)
+    candn = cand.numpy()
+    term = np.where(candn, a_np * eps_a / np.maximum(1.0 - a_np, 1e-300) + 2 * U32, 0.0)
+    rho = np.cumsum(term, axis=1)
     Tn = T_after.detach().numpy()
-    ft = exam & cand.numpy() & (np.abs(Tn / T_MIN - 1.0) < flag_tol_T)
+    ft = exam & candn & (np.abs(Tn / T_MIN - 1.0) < FLAG_SAFETY * rho + T_MIN_F32_REL)
     flag = fa.any(1) | ft.any(1)
     return out, T_final, stop, n_exam, n_contrib, flag
 
@@ -183,14 +246,15 @@ def tile_pixels(t, grid_x, tile_w, tile_h, width, height):
 
 
 def rasterize(rec, lists, width, height, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0),
-              tiles=None, d_image=None):
+              tiles=None, d_image=None, rec_delta=None):
     """Render one view from projected records.
 
     rec: dict of torch float64 tensors mean2d [N,2], conic_f [N,3], opacity [N],
     rgb [N,3] (leaves that may require grad). lists: {tile: record indices in
     depth order} (see tile_lists). tiles: subset of tiles to render (default all).
     If d_image [3,H,W] is given, the vector-Jacobian product sum(image * d_image)
-    is back-propagated tile by tile into the leaves' .grad.
+    is back-propagated tile by tile into the leaves' .grad. rec_delta [N,6]: see
+    composite (widens the straddle flags for records the other side computed itself).
     Returns dict of numpy arrays image [3,H,W], T_final, stop, n_examined,
     n_contrib, flag [H,W] (only the rendered tiles are filled).
     """
@@ -212,7 +276,7 @@ def rasterize(rec, lists, width, height, tile_w=16, tile_h=16, bg=(0.0, 0.0, 0.0
         ids = torch.as_tensor(lists.get(t, np.zeros(0, np.int64)))
         out, Tf, st, ne, nc, fl = composite(
             X + 0.5, Y + 0.5, rec["mean2d"][ids], rec["conic_f"][ids], rec["opacity"][ids],
-            rec["rgb"][ids], bg)
+            rec["rgb"][ids], bg, None if rec_delta is None else np.asarray(rec_delta)[ids.numpy()])
         if dimg is not None and ids.numel() > 0:
             g = dimg[:, Y, X].T                                   # [P,3]
             s = (out * g).sum()
@@ -234,13 +298,13 @@ def records_to_torch(mean2d, conic_f, opacity, rgb, requires_grad=False):
 
 
 def raster_vjp(mean2d, conic_f, opacity, rgb, lists, width, height, d_image, tile_w=16,
-               tile_h=16, bg=(0.0, 0.0, 0.0), tiles=None):
+               tile_h=16, bg=(0.0, 0.0, 0.0), tiles=None, rec_delta=None):
     """Gradients of sum(image * d_image) w.r.t. the projected records (FP64).
 
     Returns (render dict, grads dict with d_mean2d [N,2], d_conic [N,3] (w.r.t.
     (A, beta, gamma)), d_opacity [N], d_rgb [N,3])."""
     rec = records_to_torch(mean2d, conic_f, opacity, rgb, requires_grad=True)
-    out = rasterize(rec, lists, width, height, tile_w, tile_h, bg, tiles, d_image)
+    out = rasterize(rec, lists, width, height, tile_w, tile_h, bg, tiles, d_image, rec_delta)
     g = {}
     for k, name in (("mean2d", "d_mean2d"), ("conic_f", "d_conic"), ("opacity", "d_opacity"),
                     ("rgb", "d_rgb")):

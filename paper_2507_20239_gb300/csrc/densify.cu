@@ -400,7 +400,8 @@ SelectState *g_scratch_addr[kMaxScratchDevices] = {};
 
 // Device address of g_select_scratch on the current device. The array's name is
 // only a host-side stand-in for it, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached; the cache does not survive a
+// cudaDeviceReset of that device.
 static gs_status_t static_select_scratch(SelectState **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxScratchDevices) return GS_ERR_CUDA;

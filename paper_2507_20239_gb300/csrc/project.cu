@@ -2,7 +2,9 @@
 //
 // Forward per (view, Gaussian) record: Eq. 1's covariance Sigma = R S S^T R^T,
 // the affine projection Sigma' = J W Sigma W^T J^T (Sec. "Preliminary"), the conic
-// (Sigma' + 0.3 I)^-1, a 3-sigma extent, the pixel mean, the tile rectangle and the
+// (Sigma' + 0.3 I)^-1, the footprint where alpha can reach the 1/255 floor (the
+// ellipse d^T Sigma''^-1 d <= 2 ln(255 o); its bounding box, with the binning
+// margin, gives the extent), the pixel mean, the tile rectangle and the
 // SH-evaluated colour c_i of Eq. 2.  Backward per Gaussian: the chain rule through
 // all of the above, summed over views, with the optional densification statistic.
 #include <math.h>

@@ -82,3 +82,80 @@ def scene(name: str):
         sc.targets = [rng.uniform(0, 1, (3, c.height, c.width)).astype(np.float32) for c in cams]
         return sc
     raise KeyError(name)
+
+
+def exact_list_check(mean2d, conic_f, q_max, radius, width, height, tile, list_tiles, list_recs,
+                     chunk=200_000):
+    """The FP32 tile lists of one view against the exact FP64 footprint geometry.
+
+    For every visible record, the candidate tiles are those under its FP64 footprint
+    box (half-extents from the conic, grown by a pixel), and each (tile, record) pair
+    is decided by the exact box-minimum test (oracle.project.tile_hit, FP64) with the
+    FP32 decision's derived margin (oracle.project.band_margin):
+      must = the pair is kept with the box shrunk by delta and bound qb (1 - eps);
+      may  = the pair is kept with the box grown by delta and bound qb (1 + eps).
+    Asserts that every `must` pair is in the lists and every listed pair is `may`.
+    list_tiles / list_recs: the listed pairs (view-local tile index, record index).
+    Returns (listed, must, between) pair counts.
+    """
+    from oracle import project as oproj
+    tw, th = tile
+    gx, gy = oproj.tile_grid(width, height, tw, th)
+    n = mean2d.shape[0]
+    listed = np.unique(np.asarray(list_tiles, np.int64) * n + np.asarray(list_recs, np.int64))
+    vis = np.nonzero(np.asarray(radius) > 0)[0]
+    n_must = n_between = 0
+    may_keys = []
+    for c0 in range(0, vis.size, chunk):
+        r = vis[c0:c0 + chunk]
+        u = mean2d[r, 0].astype(np.float64)
+        v = mean2d[r, 1].astype(np.float64)
+        A, beta, gamma = (conic_f[r, k].astype(np.float64) for k in range(3))
+        qb = q_max[r].astype(np.float64) * oproj.BIN_MARGIN
+        hx = np.sqrt(qb * (1.0 / A + beta * beta / gamma))
+        hy = np.sqrt(qb / gamma)
+        x0 = np.clip(np.floor((u - hx - 1.0) / tw), 0, gx).astype(np.int64)
+        x1 = np.clip(np.floor((u + hx + 1.0) / tw) + 1, 0, gx).astype(np.int64)
+        y0 = np.clip(np.floor((v - hy - 1.0) / th), 0, gy).astype(np.int64)
+        y1 = np.clip(np.floor((v + hy + 1.0) / th) + 1, 0, gy).astype(np.int64)
+        w = np.maximum(x1 - x0, 0)
+        cnt = w * np.maximum(y1 - y0, 0)
+        j = np.repeat(np.arange(r.size), cnt)
+        local = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        tx = x0[j] + local % w[j]
+        ty = y0[j] + local // w[j]
+        X0 = tx * tw + 0.5
+        X1 = np.minimum((tx + 1) * tw, width) - 0.5
+        Y0 = ty * th + 0.5
+        Y1 = np.minimum((ty + 1) * th, height) - 0.5
+        delta, eps = oproj.band_margin(u[j], v[j], beta[j], hx[j], hy[j], width, height)
+        args = (u[j], v[j], A[j], beta[j], gamma[j])
+        must = oproj.tile_hit(*args, qb[j] * (1 - eps), X0 + delta, X1 - delta, Y0 + delta, Y1 - delta)
+        may = oproj.tile_hit(*args, qb[j] * (1 + eps), X0 - delta, X1 + delta, Y0 - delta, Y1 + delta)
+        key = (ty * gx + tx) * n + r[j]
+        mk = key[must]
+        pos = np.searchsorted(listed, mk)
+        found = (pos < listed.size) & (listed[np.minimum(pos, listed.size - 1)] == mk)
+        assert found.all(), f"{(~found).sum()} pairs the exact test keeps are missing, e.g. " \
+                            f"(tile, record) {[(int(k // n), int(k % n)) for k in mk[~found][:4]]}"
+        n_must += int(must.sum())
+        n_between += int((may & ~must).sum())
+        may_keys.append(key[may])
+    may_keys = np.unique(np.concatenate(may_keys)) if may_keys else np.zeros(0, np.int64)
+    pos = np.searchsorted(may_keys, listed)
+    ok = (pos < may_keys.size) & (may_keys[np.minimum(pos, max(may_keys.size - 1, 0))] == listed)
+    assert ok.all(), f"{(~ok).sum()} listed pairs lie outside the exact footprint, e.g. " \
+                     f"(tile, record) {[(int(k // n), int(k % n)) for k in listed[~ok][:4]]}"
+    return int(listed.size), n_must, n_between
+
+
+def bins_pairs(bins, n_tiles):
+    """(tile, record) of every listed entry of a Bins, on the host."""
+    ranges = bins.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    M = int(bins.count.item())
+    vals = bins.vals[:M].cpu().numpy().view(np.uint32).astype(np.int64)
+    lens = ranges[:n_tiles, 1] - ranges[:n_tiles, 0]
+    tiles = np.repeat(np.arange(n_tiles, dtype=np.int64), lens)
+    starts = np.repeat(ranges[:n_tiles, 0], lens)
+    pos = starts + (np.arange(lens.sum()) - np.repeat(np.cumsum(lens) - lens, lens))
+    return tiles, vals[pos]

@@ -8,7 +8,7 @@ from oracle import project as oproj
 from oracle import raster as oras
 from paper_2507_20239_gb300 import rasterizer as R
 from paper_2507_20239_gb300 import synth
-from tests.gs_fixtures import oracle_records_fp32, records_to_gpu, scene
+from tests.gs_fixtures import bins_pairs, dev_params, exact_list_check, oracle_records_fp32, records_to_gpu, scene
 
 pytestmark = pytest.mark.gpu
 
@@ -139,3 +139,22 @@ def test_bin_sort_full_size_orbit_scene():
     rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam)
     M = _check([rec], [cam], (16, 16))
     assert M > 1_000_000
+
+
+def test_full_view_lists_hold_every_exact_fp64_pair():
+    """The benchmark view's lists, made by the GPU path end to end (gs_project then
+    gs_bin_sort), against the exact FP64 geometry of the footprint ellipse on the
+    GPU's own FP32 records: every (tile, record) pair the exact test keeps beyond the
+    derived FP32 margin is listed, and every listed pair lies within it."""
+    sc = scene("orbit")
+    cam = sc.cameras[0]
+    frame = R.Frame([cam])
+    proj = R.project(dev_params(sc), sc.sh_degree, frame)
+    bins = R.bin_sort(proj, frame)
+    torch.cuda.synchronize()
+    co = proj.conic_opacity.cpu().numpy()
+    tiles, recs = bins_pairs(bins, frame.n_tiles)
+    listed, must, between = exact_list_check(proj.mean2d.cpu().numpy(), co[:, :3], proj.rgb[:, 3].cpu().numpy(),
+                                             proj.radius.cpu().numpy(), cam.width, cam.height, (16, 16), tiles, recs)
+    print(f"listed {listed}, exact-with-margin {must}, within the margin {between}")
+    assert listed > 10_000_000 and must > 0.99 * listed and between < 1e-3 * listed

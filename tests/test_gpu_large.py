@@ -8,7 +8,7 @@ import torch
 
 from paper_2507_20239_gb300 import rasterizer as R
 from paper_2507_20239_gb300 import synth
-from tests.gs_fixtures import oracle_records_fp32, rel_l2
+from tests.gs_fixtures import bins_pairs, exact_list_check, oracle_records_fp32, rel_l2
 from tests.test_gpu_project import _compare_projection
 from tests.test_gpu_raster import GRAD_TOL, _compare_fwd, _gpu, _oracle_fwd, _tile_mask
 
@@ -26,6 +26,31 @@ def test_large_projection_sampled(large):
     _compare_projection(large, large.cameras, sample=sample)
 
 
+def test_large_lists_hold_every_exact_fp64_pair(large):
+    """The four-view frame of the large scene binned in one launch (the benchmark's
+    configuration), views 0 and 3 against the exact FP64 footprint geometry of the
+    GPU's own records (see tests/gs_fixtures.exact_list_check)."""
+    frame = R.Frame(large.cameras)
+    P = R.to_device_params(large.params(), "cuda")
+    proj = R.project(P, large.sh_degree, frame)
+    bins = R.bin_sort(proj, frame)
+    torch.cuda.synchronize()
+    tiles, recs = bins_pairs(bins, frame.n_tiles)
+    del bins
+    n = large.n
+    for v in (0, 3):
+        W, H, _, toff, gx = frame.views[v][:5]
+        nt = gx * ((H + 15) // 16)
+        sel = (tiles >= toff) & (tiles < toff + nt)
+        sl = slice(v * n, (v + 1) * n)
+        co = proj.conic_opacity[sl].cpu().numpy()
+        listed, must, between = exact_list_check(
+            proj.mean2d[sl].cpu().numpy(), co[:, :3], proj.rgb[sl, 3].cpu().numpy(), proj.radius[sl].cpu().numpy(),
+            W, H, (16, 16), tiles[sel] - toff, recs[sel] - v * n)
+        print(f"view {v}: listed {listed}, exact-with-margin {must}, within the margin {between}")
+        assert listed > 1_000_000 and between < 1e-3 * listed
+
+
 def test_large_view_raster_recomputed_stop_sampled_tiles(large):
     cam = large.cameras[0]
     tile = (16, 16)
@@ -39,8 +64,9 @@ def test_large_view_raster_recomputed_stop_sampled_tiles(large):
     mask = _tile_mask(cam, tile, tiles)
     d_image = np.where(mask[None], rng.normal(0, 1, (3, cam.height, cam.width)), 0).astype(np.float32)
     o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
+    counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
-                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, max_flag_frac=5e-2)
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts, max_flag_frac=5e-3)
     rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda(), stop=None)
     torch.cuda.synchronize()
     got = dict(d_mean2d=rg.d_mean2d.cpu().numpy(), d_conic=rg.d_conic_opacity[:, :3].cpu().numpy(),

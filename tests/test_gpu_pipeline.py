@@ -8,12 +8,12 @@ import torch
 from oracle import pipeline as opipe
 from paper_2507_20239_gb300 import rasterizer as R
 from paper_2507_20239_gb300.autograd import DensifyStats, rasterize
-from tests.gs_fixtures import dev_params, rel_l2, scene
+from tests.gs_fixtures import bins_pairs, dev_params, rel_l2, scene
 
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_view(sc, cams, targets, tile=(16, 16), bg=(0, 0, 0)):
+def _gpu_view(sc, cams, targets, tile=(16, 16), bg=(0, 0, 0), want_bins=False):
     frame = R.Frame(cams, tile=tile)
     P = dev_params(sc)
     proj = R.project(P, sc.sh_degree, frame)
@@ -24,26 +24,85 @@ def _gpu_view(sc, cams, targets, tile=(16, 16), bg=(0, 0, 0)):
     rg = R.raster_bwd(proj, bins, frame, img, d_img, bg)
     g = R.project_bwd(P, sc.sh_degree, frame, proj, rg)
     torch.cuda.synchronize()
+    if want_bins:
+        return frame, proj, img, loss, g, bins
     return frame, proj, img, loss, g
+
+
+def _explain_list_difference(t, gpu_list, orc_list, o64, frame, cam):
+    """Why one tile's lists differ between the GPU path (its own FP32 records) and the
+    oracle (FP64 records): every record listed on one side only must lie on the
+    footprint boundary (the exact box minimum of q within 1e-4 relative of the
+    bound), and the common records' GPU order may only swap records whose FP64
+    depths are within 64 FP32 ulps (the GPU's depth carries the rounding of R mu + t
+    in FP32, the oracle's one rounding of the FP64 value)."""
+    from oracle import project as oproj
+    only = np.setxor1d(gpu_list, orc_list)
+    if only.size:
+        gx = frame.views[0][4]
+        tx, ty = t % gx, t // gx
+        X0, Y0 = tx * 16 + 0.5, ty * 16 + 0.5
+        X1, Y1 = min((tx + 1) * 16, cam.width) - 0.5, min((ty + 1) * 16, cam.height) - 0.5
+        cf = o64["conic_f"][only]
+        qmin = oproj.box_min_q(o64["mean2d"][only, 0], o64["mean2d"][only, 1],
+                               oproj.expand_conic(cf[:, 0], cf[:, 1], cf[:, 2]), X0, X1, Y0, Y1)
+        qb = o64["q_max"][only] * oproj.BIN_MARGIN
+        assert np.all(np.abs(qmin / qb - 1) < 1e-4), (t, only, qmin / qb)
+    g = np.asarray(gpu_list)[np.isin(gpu_list, orc_list)]
+    d = o64["depth"][g]
+    ulp = np.spacing(d.astype(np.float32)).astype(np.float64)
+    assert np.all(np.diff(d) >= -64 * ulp[1:]), t
+    return int(only.size)
 
 
 @pytest.mark.parametrize("name", ["small", "orbit_small"])
 def test_end_to_end_view_matches_oracle(name):
+    """Both sides project on their own (FP32 on the GPU, FP64 in the oracle). Every
+    pixel is held to 1e-4 except (a) pixels of tiles whose lists differ, each
+    difference shown to be a rounding straddle (a record on the footprint boundary,
+    or two records at the same depth to within FP32 rounding), and (b) pixels the
+    oracle flags, its FP32 straddle window widened by the measured differences
+    between the two sides' records."""
+    from oracle import project as oproj
     sc = scene(name)
     cam = sc.cameras[0]
-    frame, proj, img, loss, g = _gpu_view(sc, [cam], sc.targets)
-    o = opipe.render_view(sc.params(), sc.sh_degree, cam, target=sc.targets[0])
+    frame, proj, img, loss, g, bins = _gpu_view(sc, [cam], sc.targets, want_bins=True)
+    # the records' differences, as absolute (u, v, A, beta, gamma, o)
+    o64 = oproj.project_np(sc.params(), sc.sh_degree, cam)
+    co = proj.conic_opacity.cpu().numpy().astype(np.float64)
+    m2 = proj.mean2d.cpu().numpy().astype(np.float64)
+    delta = np.abs(np.concatenate([m2 - o64["mean2d"], co[:, :3] - o64["conic_f"],
+                                   co[:, 3:4] - o64["opacity"][:, None]], 1))
+    vis = o64["visible"]
+    delta[~vis] = 0
+    o = opipe.render_view(sc.params(), sc.sh_degree, cam, target=sc.targets[0], rec_delta=delta)
     r = o["render"]
-    # records whose integer footprint decisions straddle a rounding boundary may
-    # legitimately differ between FP32 and FP64; they must be rare
     rad_g = proj.radius.cpu().numpy()
-    diff_rec = (rad_g != o["proj"]["radius"]).sum()
+    diff_rec = int((rad_g != o["proj"]["radius"]).sum())
     assert diff_rec <= max(1, 1e-4 * sc.n), diff_rec
+    # tiles whose lists (records and order) differ between the two sides
+    tiles, recs = bins_pairs(bins, frame.n_tiles)
+    gx = frame.views[0][4]
+    same_list = np.ones((cam.height, cam.width), bool)
+    n_diff_tiles = n_boundary = 0
+    starts = np.searchsorted(tiles, np.arange(frame.n_tiles + 1))
+    for t in range(frame.n_tiles):
+        gl, ol = recs[starts[t]:starts[t + 1]], o["lists"].get(t, np.zeros(0, np.int64))
+        if not np.array_equal(gl, ol):
+            n_diff_tiles += 1
+            n_boundary += _explain_list_difference(t, gl, ol, o64, frame, cam)
+            tx, ty = t % gx, t // gx
+            same_list[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = False
     gimg = frame.view_image(img, 0).cpu().numpy()
     err = np.abs(gimg - r["image"]).max(0)
-    ok = ~r["flag"]
-    frac_bad = (err[ok] >= 1e-4).mean()
-    assert frac_bad < 1e-3, (frac_bad, err.max())
+    ok = ~r["flag"] & same_list
+    n_flag = int((r["flag"] & same_list).sum())
+    print(f"tiles with differing lists {n_diff_tiles} of {frame.n_tiles} (boundary records {n_boundary}); "
+          f"flagged pixels {n_flag}; records with differing radius {diff_rec}; max err elsewhere "
+          f"{err[ok].max():.2e}")
+    assert n_diff_tiles <= max(1, 0.05 * frame.n_tiles), n_diff_tiles
+    assert n_flag <= max(2, 2e-3 * ok.size), n_flag
+    assert err[ok].max() < 1e-4, err[ok].max()
     assert abs(float(loss[0]) - o["loss"]) < 1e-5
     for k in R.PARAM_KEYS:
         e = rel_l2(g[k].cpu().numpy(), o["param_grads"][k])

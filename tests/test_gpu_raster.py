@@ -47,27 +47,38 @@ def _tile_mask(cam, tile, tiles):
     return m
 
 
-def _compare_fwd(o, img, T, stop, mask=None, counts=None, max_flag_frac=1e-2):
+def _compare_fwd(o, img, T, stop, mask=None, counts=None, max_flag_frac=2e-3):
     """Image and T within 1e-4, stop index and per-pixel work counts exact, on every
-    pixel the oracle does not flag; flagged pixels (a cut-off decision within the
-    FP32 error bound of its threshold) must be rare and within 1/255 + 1e-4.
-    The expected flagged fraction grows with the entries a pixel examines (each has
-    a ~1e-6 chance of lying inside the alpha-floor window), hence the larger cap for
-    the dense full-size tiles."""
+    pixel the oracle does not flag. A flagged pixel (an alpha-floor or cut-off
+    decision within the derived FP32 error bound of its threshold, see
+    oracle.raster.composite) whose GPU stop index and work counts still equal the
+    oracle's took the same decisions and is held to 1e-4 too; the others (a decision
+    flipped inside the bound) to 1/255 + 1e-4. Flagged pixels must be rare: the
+    derived window predicts ~0.02% on the 60k-Gaussian view and ~0.2% on the dense
+    tiles of the full-size views."""
     flag = o["flag"]
     sel = ~flag if mask is None else (~flag & mask)
     err = np.abs(img - o["image"]).max(0)
-    assert err[sel].max() < IMG_TOL, err[sel].max()
-    assert np.abs(T - o["T_final"])[sel].max() < IMG_TOL
+    errT = np.abs(T - o["T_final"])
+    assert err[sel].max(initial=0) < IMG_TOL, err[sel].max()
+    assert errT[sel].max(initial=0) < IMG_TOL
     assert np.array_equal(stop[sel], o["stop"][sel])
     if counts is not None:
         assert np.array_equal(counts[..., 0][sel], o["n_examined"][sel])
         assert np.array_equal(counts[..., 1][sel], o["n_contrib"][sel])
     fl = flag if mask is None else (flag & mask)
-    assert fl.sum() <= max(2, max_flag_frac * (sel.sum() + fl.sum())), fl.sum()
-    if fl.sum():
+    n_fl = int(fl.sum())
+    print(f"flagged {n_fl} of {int(sel.sum()) + n_fl} pixels")
+    assert n_fl <= max(2, max_flag_frac * (sel.sum() + n_fl)), n_fl
+    if n_fl:
+        same = fl & (stop == o["stop"])
+        if counts is not None:
+            same &= (counts[..., 0] == o["n_examined"]) & (counts[..., 1] == o["n_contrib"])
+        else:
+            same[:] = False
+        assert err[same].max(initial=0) < IMG_TOL and errT[same].max(initial=0) < IMG_TOL
         assert err[fl].max() < 1 / 255 + IMG_TOL
-    return int(fl.sum())
+    return n_fl
 
 
 @pytest.mark.parametrize("name,tile,bg", [("small", (16, 16), (0, 0, 0)), ("small", (8, 8), (0.2, 0.5, 1.0)),
@@ -109,7 +120,7 @@ def test_raster_bwd_matches_oracle(name, tile, bg, use_stop):
     rng = np.random.default_rng(7)
     d_image = rng.normal(0, 1, (3, cam.height, cam.width)).astype(np.float32)
     o, g = _oracle_fwd(rec, cam, tile, bg, d_image=d_image)
-    assert o["flag"].sum() <= max(2, 1e-2 * o["flag"].size)
+    assert o["flag"].sum() <= max(2, 2e-3 * o["flag"].size)
     dg = torch.as_tensor(d_image.reshape(-1)).cuda()
     rg = R.raster_bwd(proj, bins, frame, img, dg, bg, stop=stop if use_stop else None)
     torch.cuda.synchronize()
@@ -143,7 +154,7 @@ def test_raster_full_size_sampled_tiles():
     o, g = _oracle_fwd(rec, cam, tile, (0, 0, 0), tiles=tiles, d_image=d_image)
     counts = R.raster_count(proj, bins, frame).cpu().numpy().reshape(cam.height, cam.width, 2)
     _compare_fwd(o, frame.view_image(img, 0).cpu().numpy(), frame.view_pixels(T, 0).cpu().numpy(),
-                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts, max_flag_frac=5e-2)
+                 frame.view_pixels(stop, 0).cpu().numpy(), mask=mask, counts=counts, max_flag_frac=5e-3)
     for st in (None, stop):   # recomputed cut-off, and the forward's stop indices (the bench's path)
         rg = R.raster_bwd(proj, bins, frame, img, torch.as_tensor(d_image.reshape(-1)).cuda(), stop=st)
         torch.cuda.synchronize()

@@ -56,7 +56,7 @@ def test_splat_bwd_matches_oracle(name, tile, bg):
     rng = np.random.default_rng(7)
     d_image = rng.normal(0, 1, (3, cam.height, cam.width)).astype(np.float32)
     o, g = _oracle_vjp(rec, cam, tile, bg, d_image)
-    assert o["flag"].sum() <= max(2, 1e-2 * o["flag"].size)
+    assert o["flag"].sum() <= max(2, 2e-3 * o["flag"].size)
     dg = torch.as_tensor(d_image.reshape(-1)).cuda()
     rs = R.raster_bwd_splat(proj, bins, frame, img, dg, stop, ckpt)
     rp = R.raster_bwd(proj, bins, frame, img, dg, bg, stop=stop)

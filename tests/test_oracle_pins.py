@@ -298,6 +298,65 @@ def test_band_hit_equals_box_minimum_test_in_fp64():
     assert np.array_equal(a[~near], b[~near])
 
 
+def test_fp32_band_decision_within_derived_margin_of_exact_test():
+    # The FP32 binning decision (band_span in FP32, the procedure the CUDA lists
+    # follow) against the exact FP64 box-minimum test, at the coordinate magnitudes
+    # of a 2048-pixel frame: every box the exact test keeps with the derived margin
+    # (box shrunk by delta, bound qb (1 - eps)) is kept in FP32, and every box FP32
+    # keeps is kept exactly once grown by delta with bound qb (1 + eps).
+    rng = np.random.default_rng(15)
+    n = 200_000
+    W, H = 2048, 1400
+    cf = _rand_conic_f(rng, n)
+    # elongated splats too: beta up to ~10
+    cf[: n // 4, 1] *= rng.uniform(1, 10, n // 4)
+    qb = rng.uniform(0.5, 12, n)
+    X0 = rng.integers(0, W // 16, n) * 16 + 0.5
+    Y0 = rng.integers(0, H // 16, n) * 16 + 0.5
+    X1, Y1 = X0 + 15.0, Y0 + 15.0
+    # means within a few footprint radii of the box
+    half = oproj.footprint_half(cf, qb / oproj.BIN_MARGIN)
+    u = X0 + rng.uniform(-1.5, 2.5, n) * (half[:, 0] + 8)
+    v = Y0 + rng.uniform(-1.5, 2.5, n) * (half[:, 1] + 8)
+    f32 = lambda x: np.asarray(x, np.float32)
+    u, v, qb = f32(u).astype(np.float64), f32(v).astype(np.float64), f32(qb).astype(np.float64)
+    cf = f32(cf).astype(np.float64)
+    got = oproj.band_hit(f32(u), f32(v), f32(cf[:, 0]), f32(cf[:, 1]), f32(cf[:, 2]), f32(qb),
+                         f32(X0), f32(X1), f32(Y0), f32(Y1))
+    delta, eps = oproj.band_margin(u, v, cf[:, 1], half[:, 0], half[:, 1], W, H)
+    must = oproj.tile_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb * (1 - eps),
+                          X0 + delta, X1 - delta, Y0 + delta, Y1 - delta)
+    may = oproj.tile_hit(u, v, cf[:, 0], cf[:, 1], cf[:, 2], qb * (1 + eps),
+                         X0 - delta, X1 + delta, Y0 - delta, Y1 + delta)
+    assert 0.1 * n < must.sum() and may.sum() < 0.9 * n
+    assert not np.any(must & ~got), np.nonzero(must & ~got)[0][:5]
+    assert not np.any(got & ~may), np.nonzero(got & ~may)[0][:5]
+    # the margin is tight enough to mean something: few boxes fall between
+    assert (may & ~must).sum() < 1e-3 * n
+
+
+def test_box_min_q_brute_force():
+    # the exact box minimum against a fine grid search over the box, and its
+    # special cases: mean inside -> 0; axis-aligned -> separable closed form
+    rng = np.random.default_rng(16)
+    for _ in range(200):
+        a, c = rng.uniform(0.05, 2, 2)
+        b = rng.uniform(-0.95, 0.95) * math.sqrt(a * c)
+        u, v = rng.uniform(-10, 30, 2)
+        X0, Y0 = rng.uniform(0, 10, 2)
+        X1, Y1 = X0 + rng.uniform(1, 12), Y0 + rng.uniform(1, 12)
+        got = float(oproj.box_min_q(u, v, (a, b, c), X0, X1, Y0, Y1))
+        xs, ys = np.meshgrid(np.linspace(X0, X1, 801), np.linspace(Y0, Y1, 801))
+        dx, dy = u - xs, v - ys
+        brute = (a * dx * dx + 2 * b * dx * dy + c * dy * dy).min()
+        assert got <= brute + 1e-12
+        assert brute - got <= 2e-3 * (1 + brute)
+    assert oproj.box_min_q(5.0, 5.0, (1.0, 0.3, 2.0), 0.5, 10.5, 0.5, 10.5) == 0.0
+    # b = 0: q = a dist_x^2 + c dist_y^2 with the per-axis distances to the box
+    assert math.isclose(float(oproj.box_min_q(20.0, -3.0, (0.5, 0.0, 2.0), 0.5, 10.5, 0.5, 10.5)),
+                        0.5 * 9.5 ** 2 + 2.0 * 3.5 ** 2)
+
+
 def test_band_span_closed_form_axis_aligned():
     # beta = 0: the ellipse x^2 A + y^2 gamma <= qb; over a band containing dy = 0 the
     # extent is u +- sqrt(qb / A); over a band at distance h it is u +- sqrt((qb - gamma h^2) / A)
@@ -736,3 +795,20 @@ def test_anisotropic_footprint_matches_inverse_covariance():
     a = np.minimum(0.99, o * np.exp(-0.5 * q))
     a = np.where(a >= 1 / 255, a, 0.0)                  # the tile lists lose no such pixel
     assert np.abs(res["render"]["image"][0] - c * a).max() < 1e-13
+
+
+def test_fp32_band_lists_hold_every_exact_pair():
+    # the tile lists of the FP32 decision procedure (band_span over the FP32 tile
+    # rectangle), on a 60k-Gaussian view, against the exact FP64 box-minimum test
+    # with the derived margin: nothing the exact test keeps is missing, nothing
+    # listed lies outside
+    from tests.gs_fixtures import exact_list_check, oracle_lists, oracle_records_fp32, scene
+    sc = scene("orbit_small")
+    cam = sc.cameras[0]
+    rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam)
+    lists = oracle_lists(rec)
+    tiles = np.concatenate([np.full(len(l), t) for t, l in lists.items()])
+    recs = np.concatenate([l for l in lists.values()])
+    listed, must, between = exact_list_check(rec["mean2d"], rec["conic_f"], rec["q_max"], rec["radius"],
+                                             cam.width, cam.height, (16, 16), tiles, recs)
+    assert listed > 50_000 and must > 0.99 * listed and between < 1e-3 * listed
