@@ -236,22 +236,37 @@ gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs
  * buckets of 32 entries, one lane per entry, and the tile's pixels flow through
  * each bucket from a checkpoint the forward stored at its first position.
  *
- * gs_raster_ckpt_size: bytes of the checkpoint buffer for a frame whose lists hold
- * at most `capacity` entries (the gs_bins_t capacity): (ceil(capacity / 32) +
- * n_tiles) * tile_w * tile_h * 16; 0 for an invalid frame or capacity.
+ * Checkpoints are stored per (bucket, 8 x 8 pixel block) that the forward actually
+ * walks, in 1 KB slots (64 pixels x float4); a table of 4 bytes per possible
+ * (bucket, block) pair locates them. The slot count is the caller's choice: a
+ * buffer with a slot for every pair cannot overflow; a smaller one (sized from a
+ * measured gs_raster_ckpt_usage with headroom, as the duplicate capacity is) holds
+ * only the walked pairs, and a forward that needs more reports it through
+ * gs_raster_ckpt_usage and leaves the excess pairs without checkpoints (the
+ * backward then treats them as T = 1, so the gradients are wrong until the caller
+ * grows the buffer and runs the step again).
+ *
+ * gs_raster_ckpt_size: bytes of a checkpoint buffer with n_slots slots for a frame
+ * whose lists hold at most `capacity` entries (the gs_bins_t capacity); n_slots < 0
+ * gives a slot for every (bucket, block) pair, (ceil(capacity / 32) + n_tiles) x
+ * tile_w tile_h / 64. 0 for an invalid frame or capacity.
  *
  * gs_raster_fwd_ckpt: gs_raster_fwd that always writes stop [n_pixels] and also,
  * for every pixel still compositing at list position 32 b of its tile, the float4
  * (T, R, G, B) of the state before that position (transmittance and the colour
- * composited so far) into ckpt. ckpt: device, 16-byte aligned, at least
- * gs_raster_ckpt_size(frame, bins->capacity) bytes, else GS_ERR_INVALID_ARG;
- * layout is private to the pair of calls (entries of pixels that had stopped are
- * left unwritten).
+ * composited so far) into ckpt. ckpt: device, 16-byte aligned, ckpt_bytes at least
+ * gs_raster_ckpt_size(frame, bins->capacity, 0); its slot count is what the bytes
+ * beyond that hold. Layout is private to these calls.
+ *
+ * gs_raster_ckpt_usage: d_usage [2] (device int64) <- (slots the last
+ * gs_raster_fwd_ckpt on this buffer needed, 1 if it ran out of slots else 0).
  *
  * gs_raster_bwd_splat: gradient of Eq. 2 from the image, stop and ckpt of the
  * gs_raster_fwd_ckpt call on the same bins; dL/dsigma as in gs_raster_bwd.
  * OVERWRITES grads (clears, then accumulates once per (tile, list entry)). */
-size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity);
+size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity, int64_t n_slots);
+gs_status_t gs_raster_ckpt_usage(const gs_frame_t *frame, int64_t capacity, const void *ckpt,
+                                 size_t ckpt_bytes, int64_t *d_usage, gs_stream_t stream);
 gs_status_t gs_raster_fwd_ckpt(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                                const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
                                void *ckpt, size_t ckpt_bytes, gs_stream_t stream);
@@ -355,17 +370,30 @@ typedef struct {
   float *sh;
 } gs_params_out_t;
 
+/* Per-Gaussian provenance carried through compaction (the split/clone analysis of
+ * Sec. "Global-to-local framework"): origin = index of the Gaussian of the initial
+ * set a row descends from, splits / clones = how many split / clone operations lie
+ * on its lineage. Survivors keep their values; the copy a clone adds inherits its
+ * parent's and adds 1 to clones; both children of a split inherit the parent's and
+ * add 1 to splits. Inputs have n rows, outputs out_capacity rows (device int32). */
+typedef struct {
+  const int32_t *origin_in, *splits_in, *clones_in;
+  int32_t *origin_out, *splits_out, *clones_out;
+} gs_provenance_t;
+
 /* Densify + prune + compaction. Output rows: survivors (kept, not split) in
  * original order, then clones in parent order, then split children in parent order
  * (child 0, child 1); a row is kept iff its (inherited) logit >= *d_tau_logit.
  * Child: log-scale - FP32(log 1.6), mean + R(q) (exp(s) * z), z ~ N(0, I) from
  * Philox4x32-10 (Salmon et al., SC'11) with counter (parent, 0, event, child) and key
- * (seed), Box-Muller on u = ((x >> 8) + 0.5) 2^-24. If the new count exceeds
- * out_capacity, GS_ERR_CAPACITY is OR-ed into *d_error and nothing is written. */
+ * (seed), Box-Muller on u = ((x >> 8) + 0.5) 2^-24. prov (NULL: none) carries the
+ * provenance arrays (all six pointers set). If the new count exceeds out_capacity,
+ * GS_ERR_CAPACITY is OR-ed into *d_error and nothing is written. */
 gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in,
                              const uint8_t *split, const uint8_t *clone,
                              const float *d_tau_logit, gs_params_out_t *out,
                              const gs_extra_array_t *extra, int32_t n_extra,
+                             const gs_provenance_t *prov,
                              int64_t out_capacity, int64_t *d_new_n, int32_t *d_error,
                              void *ws, size_t ws_bytes, gs_stream_t stream);
 

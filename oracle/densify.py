@@ -140,12 +140,17 @@ def child_normals(seed: int, event: int, parent: int, child: int):
             r1 * math.cos(2.0 * math.pi * u[3]))
 
 
-def apply(params: dict, split, clone, tau_logit, seed: int, event: int, extra: dict = None):
+def apply(params: dict, split, clone, tau_logit, seed: int, event: int, extra: dict = None,
+          provenance: dict = None):
     """Densify + prune. Returns (new params dict, new extra dict, index dict).
 
     params: means, log_scales, quats, opacity_logits, sh (float32). extra: other
     per-Gaussian float arrays (e.g. optimiser moments): survivors keep their rows,
     new rows (clones, children) are zero. Child means are FP64 here.
+    provenance (optional): {origin, splits, clones} per Gaussian, for the split/clone
+    analysis of Sec. "Global-to-local framework": every output row carries its
+    parent's origin; the copy a clone adds counts one more clone, both children of
+    a split one more split; survivors keep theirs. Returned as index["provenance"].
     """
     import torch
     split = np.asarray(split, bool)
@@ -180,4 +185,9 @@ def apply(params: dict, split, clone, tau_logit, seed: int, event: int, extra: d
         e[len(surv):] = 0
         ex[k] = e
     idx = dict(survivors=surv, clones=clo, splits=spl, source=src, n_new=n_new)
+    if provenance is not None:
+        pr = {k: np.asarray(provenance[k], np.int64)[src].copy() for k in ("origin", "splits", "clones")}
+        pr["clones"][len(surv):len(surv) + len(clo)] += 1
+        pr["splits"][len(surv) + len(clo):] += 1
+        idx["provenance"] = {k: v.astype(np.int32) for k, v in pr.items()}
     return out, ex, idx

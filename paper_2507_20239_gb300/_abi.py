@@ -61,6 +61,11 @@ class GsExtraArray(C.Structure):
     _fields_ = [("src", vp), ("dst", vp), ("width", C.c_int32)]
 
 
+class GsProvenance(C.Structure):
+    _fields_ = [("origin_in", vp), ("splits_in", vp), ("clones_in", vp), ("origin_out", vp), ("splits_out", vp),
+                ("clones_out", vp)]
+
+
 class GsParamsOut(C.Structure):
     _fields_ = [("means", vp), ("log_scales", vp), ("quats", vp), ("opacity_logits", vp), ("sh", vp)]
 
@@ -88,7 +93,8 @@ SIGNATURES = {
     "gs_raster_count": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), vp, vp]),
     "gs_l1_loss_grad": (C.c_int, [P(GsFrame), vp, vp, vp, vp, vp]),
     "gs_raster_bwd": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), P(GsRasterCfg), vp, vp, vp, P(GsRecGrads), vp]),
-    "gs_raster_ckpt_size": (C.c_size_t, [P(GsFrame), C.c_int64]),
+    "gs_raster_ckpt_size": (C.c_size_t, [P(GsFrame), C.c_int64, C.c_int64]),
+    "gs_raster_ckpt_usage": (C.c_int, [P(GsFrame), C.c_int64, vp, C.c_size_t, vp, vp]),
     "gs_raster_fwd_ckpt": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), P(GsRasterCfg), vp, vp, vp, vp, C.c_size_t,
                                      vp]),
     "gs_raster_bwd_splat": (C.c_int, [P(GsProj), P(GsBins), P(GsFrame), vp, vp, vp, vp, C.c_size_t,
@@ -101,7 +107,8 @@ SIGNATURES = {
                                     C.c_size_t, vp]),
     "gs_densify_select_static": (C.c_int, [P(GsDensifyCfg), vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]),
     "gs_densify_apply": (C.c_int, [P(GsDensifyCfg), P(GsParams), vp, vp, vp, P(GsParamsOut),
-                                   P(GsExtraArray), C.c_int32, C.c_int64, vp, vp, vp, C.c_size_t, vp]),
+                                   P(GsExtraArray), C.c_int32, P(GsProvenance), C.c_int64, vp, vp, vp,
+                                   C.c_size_t, vp]),
     "gs_photometric_workspace_size": (C.c_size_t, [P(GsFrame)]),
     "gs_photometric_loss_grad": (C.c_int, [P(GsFrame), vp, vp, C.c_float, vp, vp, vp, C.c_size_t, vp]),
     "gs_adam_step": (C.c_int, [P(GsAdamCfg), P(GsParamsOut), C.c_int64, C.c_int32, P(GsParamGrads),

@@ -186,15 +186,64 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-__device__ __forceinline__ void copy_row(const float *src, float *dst, int64_t from, int64_t to, int w) {
-  for (int i = 0; i < w; ++i) dst[to * w + i] = src[from * w + i];
+// Rows [g0, g0 + cnt) of a w-wide array, copied by one warp: the batch's rows are
+// one contiguous block of the source, read coalesced; each element goes to its
+// row's survivor and clone destinations (< 0: none) and, with `children`, to both
+// rows of a split child pair. zero_new: clones and children get zeros instead (the
+// rows new Gaussians start from, e.g. optimiser moments).
+template <typename T>
+__device__ __forceinline__ void warp_copy_rows(const T *__restrict__ src, T *__restrict__ dst, int w, int64_t g0,
+                                               int cnt, const int64_t *ds, const int64_t *dc, const int64_t *dp,
+                                               bool children, bool zero_new, int lane) {
+  const int tot = cnt * w;
+  // element e = lane + 32 k sits at row e / w, column e % w; both advance by
+  // (32 / w, 32 % w) per step, wrapping the column at most once
+  const int q = 32 / w, rem = 32 - q * w;
+  int r = lane / w, c = lane - (lane / w) * w;
+  const T *s = src + g0 * w;
+  constexpr int U = 4;   // loads issued before their stores: the copy is latency-bound
+  for (int e0 = lane; e0 < tot; e0 += 32 * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = e0 + 32 * u < tot ? s[e0 + 32 * u] : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e0 + 32 * u < tot) {
+        const T nv = zero_new ? T(0) : v[u];
+        const int64_t a = ds[r], b = dc[r];
+        if (a >= 0) dst[a * w + c] = v[u];
+        if (b >= 0) dst[b * w + c] = nv;
+        if (children) {
+          const int64_t d = dp[r];
+          if (d >= 0) {
+            dst[d * w + c] = nv;
+            dst[(d + 1) * w + c] = nv;
+          }
+        }
+      }
+      r += q;
+      c += rem;
+      if (c >= w) {
+        c -= w;
+        ++r;
+      }
+    }
+  }
 }
 
-__global__ void scatter_kernel(gs_densify_cfg_t cfg, gs_params_t in, const uint8_t *__restrict__ split,
-                               const uint8_t *__restrict__ clone, const float *__restrict__ tau, gs_params_out_t out,
-                               ExtraList extra, const uint32_t *__restrict__ pos_s, const uint32_t *__restrict__ pos_c,
-                               const uint32_t *__restrict__ pos_p, const uint32_t *totals, int64_t capacity,
-                               int64_t *d_new_n, int32_t *d_error) {
+constexpr int kScatThreads = 256;
+
+// Compaction, one warp per batch of 32 consecutive Gaussians: each lane finds its
+// Gaussian's destinations (survivor row, clone row, first child row), then every
+// array is copied by the warp with coalesced reads (warp_copy_rows); split children's
+// means (Philox4x32-10 draw, Box-Muller, R(q) exp(s) z) and log-scales are computed
+// per lane.
+__global__ void __launch_bounds__(kScatThreads) scatter_kernel(
+    gs_densify_cfg_t cfg, gs_params_t in, const uint8_t *__restrict__ split, const uint8_t *__restrict__ clone,
+    const float *__restrict__ tau, gs_params_out_t out, ExtraList extra, gs_provenance_t prov,
+    const uint32_t *__restrict__ pos_s, const uint32_t *__restrict__ pos_c, const uint32_t *__restrict__ pos_p,
+    const uint32_t *totals, int64_t capacity, int64_t *d_new_n, int32_t *d_error) {
+  __shared__ int64_t s_d[kScatThreads / 32][3][32];
   const uint32_t n_s = totals[0], n_c = totals[1], n_p = totals[2];
   const int64_t new_n = (int64_t)n_s + n_c + 2ll * n_p;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -205,28 +254,48 @@ __global__ void scatter_kernel(gs_densify_cfg_t cfg, gs_params_t in, const uint8
   const float t = *tau;
   const int shw = in.sh_stride * 3;
   const float ls_div = 0.47000362924573558f;   // FP32 of log(1.6)
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < in.n; g += (int64_t)gridDim.x * blockDim.x) {
-    if (in.opacity_logits[g] < t) continue;
-    const bool sp = split[g], cl = clone[g];
-    int64_t rows[2];
-    int nrows = 0;
-    if (!sp) {
-      const int64_t o = pos_s[g];
-      copy_row(in.means, out.means, g, o, 3);
-      copy_row(in.log_scales, out.log_scales, g, o, 3);
-      copy_row(in.quats, out.quats, g, o, 4);
-      out.opacity_logits[o] = in.opacity_logits[g];
-      copy_row(in.sh, out.sh, g, o, shw);
-      for (int e = 0; e < extra.n; ++e) copy_row(extra.a[e].src, extra.a[e].dst, g, o, extra.a[e].width);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int64_t *ds = s_d[wib][0], *dc = s_d[wib][1], *dp = s_d[wib][2];
+  const int64_t n_batches = (in.n + 31) / 32;
+  for (int64_t bt = blockIdx.x * (int64_t)(kScatThreads / 32) + wib; bt < n_batches;
+       bt += (int64_t)gridDim.x * (kScatThreads / 32)) {
+    const int64_t g0 = bt * 32, g = g0 + lane;
+    const int cnt = (int)min((int64_t)32, in.n - g0);
+    bool keep = false, sp = false, cl = false;
+    if (g < in.n) {
+      keep = !(in.opacity_logits[g] < t);
+      sp = keep && split[g];
+      cl = keep && clone[g];
     }
-    if (cl) {
-      const int64_t o = (int64_t)n_s + pos_c[g];
-      copy_row(in.means, out.means, g, o, 3);
-      copy_row(in.log_scales, out.log_scales, g, o, 3);
-      copy_row(in.quats, out.quats, g, o, 4);
-      out.opacity_logits[o] = in.opacity_logits[g];
-      copy_row(in.sh, out.sh, g, o, shw);
-      rows[nrows++] = o;
+    ds[lane] = (keep && !sp) ? (int64_t)pos_s[g] : -1;
+    dc[lane] = cl ? (int64_t)n_s + pos_c[g] : -1;
+    dp[lane] = sp ? (int64_t)n_s + n_c + 2ll * pos_p[g] : -1;
+    __syncwarp();
+    warp_copy_rows(in.means, out.means, 3, g0, cnt, ds, dc, dp, false, false, lane);
+    warp_copy_rows(in.log_scales, out.log_scales, 3, g0, cnt, ds, dc, dp, false, false, lane);
+    warp_copy_rows(in.quats, out.quats, 4, g0, cnt, ds, dc, dp, true, false, lane);
+    warp_copy_rows(in.opacity_logits, out.opacity_logits, 1, g0, cnt, ds, dc, dp, true, false, lane);
+    warp_copy_rows(in.sh, out.sh, shw, g0, cnt, ds, dc, dp, true, false, lane);
+    for (int e = 0; e < extra.n; ++e)
+      warp_copy_rows(extra.a[e].src, extra.a[e].dst, extra.a[e].width, g0, cnt, ds, dc, dp, true, true, lane);
+    if (prov.origin_in != nullptr && g < in.n && keep) {
+      const int32_t po = prov.origin_in[g], ps = prov.splits_in[g], pc = prov.clones_in[g];
+      if (ds[lane] >= 0) {
+        prov.origin_out[ds[lane]] = po;
+        prov.splits_out[ds[lane]] = ps;
+        prov.clones_out[ds[lane]] = pc;
+      }
+      if (cl) {
+        prov.origin_out[dc[lane]] = po;
+        prov.splits_out[dc[lane]] = ps;
+        prov.clones_out[dc[lane]] = pc + 1;
+      }
+      if (sp)
+        for (int c = 0; c < 2; ++c) {
+          prov.origin_out[dp[lane] + c] = po;
+          prov.splits_out[dp[lane] + c] = ps + 1;
+          prov.clones_out[dp[lane] + c] = pc;
+        }
     }
     if (sp) {
       const float4 q = reinterpret_cast<const float4 *>(in.quats)[g];
@@ -235,10 +304,10 @@ __global__ void scatter_kernel(gs_densify_cfg_t cfg, gs_params_t in, const uint8
       const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                           2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                           2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
-      const float s[3] = {expf(in.log_scales[3 * g + 0]), expf(in.log_scales[3 * g + 1]),
-                          expf(in.log_scales[3 * g + 2])};
+      const float s3[3] = {expf(in.log_scales[3 * g + 0]), expf(in.log_scales[3 * g + 1]),
+                           expf(in.log_scales[3 * g + 2])};
       for (int c = 0; c < 2; ++c) {
-        const int64_t o = (int64_t)n_s + n_c + 2ll * pos_p[g] + c;
+        const int64_t o = dp[lane] + c;
         const uint4 bits = philox4x32_10(
             make_uint4((uint32_t)g, (uint32_t)((uint64_t)g >> 32), cfg.event, (uint32_t)c),
             make_uint2((uint32_t)cfg.seed, (uint32_t)(cfg.seed >> 32)));
@@ -250,22 +319,15 @@ __global__ void scatter_kernel(gs_densify_cfg_t cfg, gs_params_t in, const uint8
         float sn0, cs0, sn1, cs1;
         sincospif(2.f * u1, &sn0, &cs0);
         sincospif(2.f * u3, &sn1, &cs1);
-        const float zl[3] = {r0 * cs0 * s[0], r0 * sn0 * s[1], r1 * cs1 * s[2]};
+        const float zl[3] = {r0 * cs0 * s3[0], r0 * sn0 * s3[1], r1 * cs1 * s3[2]};
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           out.means[3 * o + i] = in.means[3 * g + i] + R[3 * i + 0] * zl[0] + R[3 * i + 1] * zl[1] + R[3 * i + 2] * zl[2];
 #pragma unroll
         for (int i = 0; i < 3; ++i) out.log_scales[3 * o + i] = __fsub_rn(in.log_scales[3 * g + i], ls_div);
-        copy_row(in.quats, out.quats, g, o, 4);
-        out.opacity_logits[o] = in.opacity_logits[g];
-        copy_row(in.sh, out.sh, g, o, shw);
-        for (int e = 0; e < extra.n; ++e)
-          for (int i = 0; i < extra.a[e].width; ++i) extra.a[e].dst[o * extra.a[e].width + i] = 0.f;
       }
     }
-    for (int k = 0; k < nrows; ++k)
-      for (int e = 0; e < extra.n; ++e)
-        for (int i = 0; i < extra.a[e].width; ++i) extra.a[e].dst[rows[k] * extra.a[e].width + i] = 0.f;
+    __syncwarp();   // the next batch rewrites this warp's destinations
   }
 }
 
@@ -348,9 +410,9 @@ extern "C" gs_status_t gs_densify_select(const gs_densify_cfg_t *cfg, const floa
 
 extern "C" gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in, const uint8_t *split,
                                         const uint8_t *clone, const float *d_tau_logit, gs_params_out_t *out,
-                                        const gs_extra_array_t *extra, int32_t n_extra, int64_t out_capacity,
-                                        int64_t *d_new_n, int32_t *d_error, void *ws, size_t ws_bytes,
-                                        gs_stream_t stream) {
+                                        const gs_extra_array_t *extra, int32_t n_extra, const gs_provenance_t *prov,
+                                        int64_t out_capacity, int64_t *d_new_n, int32_t *d_error, void *ws,
+                                        size_t ws_bytes, gs_stream_t stream) {
   if (!cfg || !in || !split || !clone || !d_tau_logit || !out || !d_new_n || !ws || in->n <= 0 ||
       in->n >= (1ll << 31) || out_capacity < 0)
     return GS_ERR_INVALID_ARG;
@@ -362,6 +424,13 @@ extern "C" gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_pa
     return GS_ERR_INVALID_ARG;
   const DensWs w = dens_layout(ws, in->n);
   if (ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
+  gs_provenance_t pv{};
+  if (prov) {
+    if (!prov->origin_in || !prov->splits_in || !prov->clones_in || !prov->origin_out || !prov->splits_out ||
+        !prov->clones_out)
+      return GS_ERR_INVALID_ARG;
+    pv = *prov;
+  }
   ExtraList el{};
   el.n = n_extra;
   for (int i = 0; i < n_extra; ++i) {
@@ -375,7 +444,9 @@ extern "C" gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_pa
     SectionFlag f{in->opacity_logits, split, clone, d_tau_logit, in->n, kind, pos, w.totals + kind};
     if (gs_status_t st = run_scan(f, w.block_sums, G, s)) return st;
   }
-  scatter_kernel<<<dgrid(in->n), kSelThreads, 0, s>>>(*cfg, *in, split, clone, d_tau_logit, *out, el, w.pos_s,
+  int sg = (int)((in->n + 32 * (kScatThreads / 32) - 1) / (32 * (kScatThreads / 32)));
+  if (sg > num_sms() * 8) sg = num_sms() * 8;
+  scatter_kernel<<<sg, kScatThreads, 0, s>>>(*cfg, *in, split, clone, d_tau_logit, *out, el, pv, w.pos_s,
                                                       w.pos_c, w.pos_p, w.totals, out_capacity, d_new_n, d_error);
   GS_LAUNCH_CHECK();
   return GS_OK;

@@ -85,6 +85,64 @@ __device__ __forceinline__ Falloff falloff(float u, float v, float a2, float bet
   return f;
 }
 
+// Packed FP32 pairs (sm_100 family: add/sub/mul/fma.rn.f32x2). Each lane of the
+// pair is one IEEE round-to-nearest operation, identical to the scalar __fadd_rn /
+// __fsub_rn / __fmul_rn / __fmaf_rn, so a packed evaluation takes exactly the
+// decisions of the scalar one; it halves the issue slots of paired FP32 work.
+__device__ __forceinline__ uint64_t f2_pack(float2 a) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+  return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// falloff() at two pixel centres of one row, (px.x, py) and (px.y, py), with packed
+// pairs: lane for lane the same operations and roundings as two falloff() calls.
+struct Falloff2 {
+  float2 t, G, raw, alpha;
+  float dy;
+};
+
+__device__ __forceinline__ Falloff2 falloff2(float u, float v, float a2, float beta, float g2, float o, float2 px,
+                                             float py) {
+  Falloff2 f;
+  const float2 dx = f2_sub(f2(u), px);
+  f.dy = __fsub_rn(v, py);
+  f.t = f2_fma(f2(beta), f2(f.dy), dx);
+  const float gdd = __fmul_rn(g2, __fmul_rn(f.dy, f.dy));
+  const float2 e = f2_fma(f2_mul(f2(a2), f.t), f.t, f2(gdd));
+  f.G = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+  f.raw = f2_mul(f2(o), f.G);
+  f.alpha = make_float2(fminf(kAlphaMax, f.raw.x), fminf(kAlphaMax, f.raw.y));
+  return f;
+}
+
 // The binning's ellipse-box test, in two steps with one IEEE FP32 rounding per
 // operation (no contraction), so that the decision is reproducible op for op:
 // band_consts_rn once per record, band_span_rn once per row of tiles (the x-extent of

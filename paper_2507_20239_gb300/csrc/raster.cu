@@ -50,6 +50,58 @@ __device__ __forceinline__ uint64_t ckpt_bucket(uint32_t list_start, uint32_t ti
   return (uint64_t)(list_start >> 5) + tile;
 }
 
+// Checkpoint buffer: only the (bucket, 8 x 8 pixel block) pairs a forward warp
+// actually walks hold data. Layout (caller-owned, sized by gs_raster_ckpt_size):
+//   pools [kCkptPools] u32       slots claimed from each pool by the last forward
+//   table [buckets x blocks] u32 slot of (bucket, block), kCkptNone past a pool's end
+//   slots [n_slots][64] float4   (T, R, G, B) of the block's 64 pixels, row-major
+// A warp claims a slot from pool (tile * blocks + block) mod n_pools, which spreads
+// the claims over n_pools counters (a power of two up to kCkptPools, about 32 of the
+// frame's blocks each, so that pools fill evenly); pool p owns slots [p P, (p + 1) P),
+// P = floor(n_slots / n_pools). A buffer with a slot for every table entry maps
+// the entry to its own slot instead (nothing can overflow; the pools still count).
+// The table needs no clearing: the backward only looks up (bucket, block) pairs
+// holding a live pixel, which the forward walked in the same frame.
+constexpr int kCkptPools = 256;
+constexpr uint32_t kCkptNone = 0xffffffffu;
+
+struct CkptLayout {
+  uint32_t *pools, *table;
+  float4 *slots;
+  uint64_t n_slots, pool_size, table_entries;
+  uint32_t n_pools;
+  size_t bytes;
+};
+
+// Pools of a frame with `blocks` 8 x 8 blocks in all: the largest power of two up to
+// kCkptPools with at least 32 blocks per pool.
+__host__ __device__ inline uint32_t ckpt_pools(uint64_t blocks) {
+  uint32_t p = 1;
+  while (p < (uint32_t)kCkptPools && (uint64_t)p * 2 * 32 <= blocks) p *= 2;
+  return p;
+}
+
+__host__ __device__ inline size_t ckpt_a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__host__ __device__ inline CkptLayout ckpt_layout(void *base, uint64_t table_entries, uint64_t n_slots,
+                                                   uint32_t n_pools = kCkptPools) {
+  CkptLayout L;
+  char *p = static_cast<char *>(base);
+  size_t off = 0;
+  L.pools = reinterpret_cast<uint32_t *>(p + off);
+  off += ckpt_a256(4 * (size_t)kCkptPools);
+  L.table = reinterpret_cast<uint32_t *>(p + off);
+  off += ckpt_a256(4 * (size_t)table_entries);
+  L.slots = reinterpret_cast<float4 *>(p + off);
+  off += (size_t)n_slots * 64 * sizeof(float4);
+  L.n_slots = n_slots;
+  L.n_pools = n_pools;
+  L.pool_size = n_slots / n_pools;
+  L.table_entries = table_entries;
+  L.bytes = off;
+  return L;
+}
+
 // Pixel mapping: warp w owns the 8x8 block (w % (TW/8), w / (TW/8)) of the tile;
 // lane l owns pixels (2 (l % 4), l / 4) and (2 (l % 4) + 1, l / 4) of that block.
 template <int TW>
@@ -121,7 +173,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
-    uint32_t *__restrict__ stop_out, float4 *__restrict__ ckpt) {
+    uint32_t *__restrict__ stop_out, CkptLayout ckpt) {
   constexpr int NW = TW * TH / 64;
   __shared__ float2 s_xy[NW][32];
   __shared__ float4 s_co[NW][32];
@@ -134,13 +186,13 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   const int py = tc.ty * TH + ly;
   const int px = tc.tx * TW + lx;
   const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
-  const float fy = (float)py + 0.5f, fx0 = (float)px + 0.5f, fx1 = (float)px + 1.5f;
+  const float fy = (float)py + 0.5f;
+  const float2 fx = f2((float)px + 0.5f, (float)px + 1.5f);
   // the warp's block of pixel centres
   const int bx = tc.tx * TW + (warp % (TW / 8)) * 8, by = tc.ty * TH + (warp / (TW / 8)) * 8;
   const float X0 = (float)bx + 0.5f, X1 = (float)min(bx + 8, tc.W) - 0.5f;
   const float Y0 = (float)by + 0.5f, Y1 = (float)min(by + 8, tc.H) - 0.5f;
-  float T0 = 1.f, T1 = 1.f;
-  float r0 = 0.f, g0 = 0.f, b0 = 0.f, r1 = 0.f, g1 = 0.f, b1 = 0.f;
+  float2 T = f2(1.f), cr = f2(0.f), cg = f2(0.f), cb = f2(0.f);   // (pixel 0, pixel 1)
   uint32_t st0 = 0, st1 = 0;
   bool done0 = !in0, done1 = !in1;
   const uint2 rg = ranges[tile];
@@ -158,10 +210,23 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
     if (CKPT) {
-      // state before list position base: (T, accumulated colour) for the per-splat backward
-      float4 *ck = ckpt + (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * (TW * TH) + ly * TW + lx;
-      if (!done0) ck[0] = make_float4(T0, r0, g0, b0);
-      if (!done1) ck[1] = make_float4(T1, r1, g1, b1);
+      // state before list position base: (T, accumulated colour) for the per-splat
+      // backward, in a slot this warp claims for (bucket, its 8 x 8 block)
+      uint32_t slot = kCkptNone;
+      if (lane == 0) {
+        const uint64_t idx = (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * NW + warp;
+        const uint32_t pool = ((uint32_t)tile * NW + warp) & (ckpt.n_pools - 1);
+        const uint32_t k = atomicAdd(ckpt.pools + pool, 1u);
+        if (ckpt.n_slots >= ckpt.table_entries) slot = (uint32_t)idx;      // room for every pair
+        else if (k < ckpt.pool_size) slot = (uint32_t)(pool * ckpt.pool_size + k);
+        ckpt.table[idx] = slot;
+      }
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot != kCkptNone) {
+        float4 *ck = ckpt.slots + (uint64_t)slot * 64 + (lane >> 2) * 8 + 2 * (lane & 3);
+        if (!done0) ck[0] = make_float4(T.x, cr.x, cg.x, cb.x);
+        if (!done1) ck[1] = make_float4(T.y, cr.y, cg.y, cb.y);
+      }
     }
     const int j = base + lane;
     const float2 xy = xy_n;
@@ -187,44 +252,33 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     }
     uint32_t b = __ballot_sync(0xffffffffu, sel);
     __syncwarp();
+    // both pixels in packed pairs, without branches: an entry a pixel skips (done,
+    // below the floor, or the one that would cross the cut-off) gets weight 0 and
+    // leaves T, the colour and the stop index as they are
     while (b) {
       const int i = __ffs(b) - 1;
       b &= b - 1u;
       const float2 xy = s_xy[warp][i];
       const float4 co = s_co[warp][i];
-      if (!done0) {
-        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx0, fy);
-        if (f.alpha >= kAlphaMin) {
-          const float Tn = __fmul_rn(T0, __fsub_rn(1.f, f.alpha));
-          if (Tn < kTMin) {
-            done0 = true;
-          } else {
-            const float4 c = s_rgb[warp][i];
-            const float w = f.alpha * T0;
-            r0 = fmaf(c.x, w, r0); g0 = fmaf(c.y, w, g0); b0 = fmaf(c.z, w, b0);
-            T0 = Tn;
-            st0 = base + i + 1;
-          }
-        }
-      }
-      if (!done1) {
-        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, fx1, fy);
-        if (f.alpha >= kAlphaMin) {
-          const float Tn = __fmul_rn(T1, __fsub_rn(1.f, f.alpha));
-          if (Tn < kTMin) {
-            done1 = true;
-          } else {
-            const float4 c = s_rgb[warp][i];
-            const float w = f.alpha * T1;
-            r1 = fmaf(c.x, w, r1); g1 = fmaf(c.y, w, g1); b1 = fmaf(c.z, w, b1);
-            T1 = Tn;
-            st1 = base + i + 1;
-          }
-        }
-      }
+      const Falloff2 f = falloff2(xy.x, xy.y, co.x, co.y, co.z, co.w, fx, fy);
+      const bool a0 = !done0 && f.alpha.x >= kAlphaMin, a1 = !done1 && f.alpha.y >= kAlphaMin;
+      const float2 Tn = f2_mul(T, f2_sub(f2(1.f), f.alpha));
+      const bool c0 = a0 && !(Tn.x < kTMin), c1 = a1 && !(Tn.y < kTMin);
+      done0 = done0 || (a0 && !c0);
+      done1 = done1 || (a1 && !c1);
+      const float2 w = f2_mul(f2(c0 ? f.alpha.x : 0.f, c1 ? f.alpha.y : 0.f), T);
+      const float4 c = s_rgb[warp][i];
+      cr = f2_fma(f2(c.x), w, cr);
+      cg = f2_fma(f2(c.y), w, cg);
+      cb = f2_fma(f2(c.z), w, cb);
+      T = f2(c0 ? Tn.x : T.x, c1 ? Tn.y : T.y);
+      st0 = c0 ? base + i + 1 : st0;
+      st1 = c1 ? base + i + 1 : st1;
     }
     __syncwarp();
   }
+  const float T0 = T.x, T1 = T.y;
+  const float r0 = cr.x, g0 = cg.x, b0 = cb.x, r1 = cr.y, g1 = cg.y, b1 = cb.y;
   const int64_t p0 = (int64_t)py * tc.W + px;
   const int64_t plane = (int64_t)tc.W * tc.H;
   float *img = image + 3 * tc.pix_off;
@@ -572,9 +626,9 @@ __global__ void __launch_bounds__(kSplatThreads, 9) raster_bwd_splat_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
-    const uint32_t *__restrict__ stop_in, const float4 *__restrict__ ckpt, float *__restrict__ g_mean2d,
+    const uint32_t *__restrict__ stop_in, const CkptLayout ckpt, float *__restrict__ g_mean2d,
     float *__restrict__ g_co, float *__restrict__ g_rgb) {
-  constexpr int NP = TW * TH, NW = kSplatThreads / 32;
+  constexpr int NP = TW * TH, NW = kSplatThreads / 32, NB = TW * TH / 64;
   static_assert(NP % 32 == 0 && NP <= 65536, "whole warps of pixels, 16-bit indices");
   __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
   __shared__ uint32_t s_stop[NP];
@@ -645,13 +699,19 @@ __global__ void __launch_bounds__(kSplatThreads, 9) raster_bwd_splat_kernel(
       nl += __popc(bal);
     }
     __syncwarp();
-    const float4 *ck = ckpt + (bk0 + (uint64_t)b) * NP;
+    // the slot of each 8 x 8 block at this bucket (lane k holds block k's); a block
+    // holding a live pixel was walked by its forward warp, so its entry is current
+    uint32_t bslot = kCkptNone;
+    if (lane < NB) bslot = ckpt.table[(bk0 + (uint64_t)b) * NB + lane];
     // live pixel `slot` for this lane: its index (-1 past the list) and checkpoint
     int pn = -1;
     float4 kn = make_float4(0.f, 0.f, 0.f, 0.f);
     auto fetch = [&](int slot) {
       pn = slot < nl ? (int)live[slot] : -1;
-      if (pn >= 0) kn = ck[pn];
+      const int px = pn & (TW - 1), py = pn / TW;
+      const uint32_t sl = __shfl_sync(0xffffffffu, bslot, (py >> 3) * (TW / 8) + (px >> 3));
+      kn = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (pn >= 0 && sl != kCkptNone) kn = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
     };
     fetch(lane);
     // ring slots 32..63 read as stopped until the second chunk replaces them: lanes
@@ -726,6 +786,229 @@ __global__ void __launch_bounds__(kSplatThreads, 9) raster_bwd_splat_kernel(
   }
 }
 
+#ifndef GS_SPLAT2_BLOCKS
+#define GS_SPLAT2_BLOCKS 7
+#endif
+constexpr int kSplat2Blocks = GS_SPLAT2_BLOCKS;   // resident CTAs per SM the register budget allows
+
+// rcp.approx.ftz.f32: the reciprocal __fdividef uses.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The per-splat backward with two live pixels per lane and step: the bucket's live
+// pixels are taken in pairs (2 i, 2 i + 1) and the pairs flow through the warp
+// diagonally as single pixels do in raster_bwd_splat_kernel (at step s lane l works on
+// pair s - l, with both pixels' (T, R) from lane l - 1). The two pixels are
+// independent, so every FP32 operation of a step is a packed pair (fma/mul/add/sub
+// .rn.f32x2), which halves the step's issue slots where the per-pixel work was one
+// scalar chain. The ring holds pairs interleaved, (a, b) in adjacent lanes of each
+// float4, so the shared-memory loads deliver packed operands directly. A pixel's
+// falloff, floor and stop decisions are the forward's own (same operations, same
+// roundings); accumulations differ from the one-pixel kernel only in summation order.
+template <int TW, int TH>
+__global__ void __launch_bounds__(kSplatThreads, kSplat2Blocks) raster_bwd_splat2_kernel(
+    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
+    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
+    int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
+    const uint32_t *__restrict__ stop_in, const CkptLayout ckpt, float *__restrict__ g_mean2d,
+    float *__restrict__ g_co, float *__restrict__ g_rgb) {
+  constexpr int NP = TW * TH, NW = kSplatThreads / 32, NB = TW * TH / 64;
+  static_assert(NP % 32 == 0 && NP <= 65536, "whole warps of pixels, 16-bit indices");
+  __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
+  __shared__ uint32_t s_stop[NP];
+  __shared__ uint16_t s_live[NW][NP];
+  // ring of pixel pairs (a, b) at pair index i % 64:
+  //   r0 = (gx_a, gx_b, gy_a, gy_b)   r1 = (gz_a, gz_b, stop_a, stop_b)
+  //   r2 = (x_a, x_b, y_a, y_b)       r3 = (T_a, T_b, R_a, R_b) at the bucket start
+  __shared__ float4 s_r0[NW][kSplatRing], s_r1[NW][kSplatRing], s_r2[NW][kSplatRing], s_r3[NW][kSplatRing];
+  __shared__ uint32_t s_max, s_next;
+  const int tile = blockIdx.x / kSplatSplit, part = blockIdx.x % kSplatSplit;
+  const TileCoord tc = tile_coord(cams, n_views, tile);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (t == 0) {
+    s_max = 0;
+    s_next = NW;
+  }
+  __syncthreads();
+  {
+    const int64_t plane = (int64_t)tc.W * tc.H;
+    const float *img = image + 3 * tc.pix_off;
+    const float *dim = d_image + 3 * tc.pix_off;
+    uint32_t mx = 0;
+    for (int p = t; p < NP; p += kSplatThreads) {
+      const int px = tc.tx * TW + p % TW, py = tc.ty * TH + p / TW;
+      uint32_t st = 0;
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (px < tc.W && py < tc.H) {
+        const int64_t q = (int64_t)py * tc.W + px;
+        st = stop_in[tc.pix_off + q];
+        g.x = dim[q]; g.y = dim[plane + q]; g.z = dim[2 * plane + q];
+        g.w = g.x * img[q] + g.y * img[plane + q] + g.z * img[2 * plane + q];
+      }
+      s_g[p] = g;
+      s_stop[p] = st;
+      mx = max(mx, st);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) atomicMax(&s_max, mx);
+  }
+  __syncthreads();
+  const uint2 rg = ranges[tile];
+  const int n = min((int)(rg.y - rg.x), (int)s_max);
+  const int nb = (n + 31) >> 5;
+  const uint64_t bk0 = ckpt_bucket(rg.x, tile);
+  uint16_t *live = s_live[warp];
+  float4 *r0 = s_r0[warp], *r1 = s_r1[warp], *r2 = s_r2[warp], *r3 = s_r3[warp];
+  for (int b = part + kSplatSplit * warp; b < nb;) {
+    const int j = 32 * b + lane;   // this lane's list position
+    const bool has = j < n;
+    uint32_t r = 0;
+    float2 xy = make_float2(0.f, 0.f);
+    float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cu = co, c = co;
+    if (has) {
+      r = vals[rg.x + j];
+      xy = mean2d[r];
+      cu = conic_o[r];
+      c = rgb[r];
+      co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
+    }
+    int nl = 0;
+    for (int p0 = 0; p0 < NP; p0 += 32) {
+      const int p = p0 + lane;
+      const bool on = s_stop[p] > (uint32_t)(32 * b);
+      const uint32_t bal = __ballot_sync(0xffffffffu, on);
+      if (on) live[nl + __popc(bal & lt)] = (uint16_t)p;
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    const int npair = (nl + 1) >> 1;
+    uint32_t bslot = kCkptNone;
+    if (lane < NB) bslot = ckpt.table[(bk0 + (uint64_t)b) * NB + lane];
+    // the pair `pair` for this lane: pixel indices (-1 past the list) and checkpoints
+    int pa = -1, pb = -1;
+    float4 ka = make_float4(1.f, 0.f, 0.f, 0.f), kb = ka;
+    auto pix_ckpt = [&](int pn) {
+      const int px = pn & (TW - 1), py = pn / TW;
+      const uint32_t sl = __shfl_sync(0xffffffffu, bslot, (py >> 3) * (TW / 8) + (px >> 3));
+      float4 k = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (pn >= 0 && sl != kCkptNone) k = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
+      return k;
+    };
+    auto fetch = [&](int pair) {
+      pa = 2 * pair < nl ? (int)live[2 * pair] : -1;
+      pb = 2 * pair + 1 < nl ? (int)live[2 * pair + 1] : -1;
+      ka = pix_ckpt(pa);
+      kb = pix_ckpt(pb);
+    };
+    fetch(lane);
+    // ring slots 32..63 read as stopped pairs until the second chunk replaces them
+    r0[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r2[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r3[32 + lane] = make_float4(1.f, 1.f, 0.f, 0.f);
+    // moments accumulated negated (see dLda below), colour terms as they are; each a
+    // (pixel a, pixel b) pair summed in the epilogue
+    float2 v0 = f2(0.f), v1 = f2(0.f), v2 = f2(0.f), v3 = f2(0.f), v4 = f2(0.f), v5 = f2(0.f);
+    float2 v6 = f2(0.f), v7 = f2(0.f), v8 = f2(0.f);
+    float2 T = f2(1.f), Rr = f2(0.f);
+    const uint32_t jj = (uint32_t)j;
+    const float2 U = f2(xy.x), V = f2(xy.y), A2 = f2(co.x), BE = f2(co.y), G2 = f2(co.z), O = f2(co.w);
+    const float2 NCX = f2(-c.x), NCY = f2(-c.y), NCZ = f2(-c.z);
+    for (int s0 = 0; s0 < npair + 31; s0 += 32) {
+      {
+        // ring slots s0 .. s0 + 31; a pixel past the list reads as stopped (stop 0)
+        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+        uint32_t sa = 0, sb = 0;
+        float xa = 0.f, ya = 0.f, xb = 0.f, yb = 0.f, ta = 1.f, tb = 1.f, ra_ = 0.f, rb_ = 0.f;
+        if (pa >= 0) {
+          ga = s_g[pa];
+          sa = s_stop[pa];
+          xa = (float)(tc.tx * TW + pa % TW) + 0.5f;
+          ya = (float)(tc.ty * TH + pa / TW) + 0.5f;
+          ta = ka.x;
+          ra_ = ga.w - (ka.y * ga.x + ka.z * ga.y + ka.w * ga.z);
+        }
+        if (pb >= 0) {
+          gb = s_g[pb];
+          sb = s_stop[pb];
+          xb = (float)(tc.tx * TW + pb % TW) + 0.5f;
+          yb = (float)(tc.ty * TH + pb / TW) + 0.5f;
+          tb = kb.x;
+          rb_ = gb.w - (kb.y * gb.x + kb.z * gb.y + kb.w * gb.z);
+        }
+        const int slot = (s0 + lane) & (kSplatRing - 1);
+        r0[slot] = make_float4(ga.x, gb.x, ga.y, gb.y);
+        r1[slot] = make_float4(ga.z, gb.z, __uint_as_float(sa), __uint_as_float(sb));
+        r2[slot] = make_float4(xa, xb, ya, yb);
+        r3[slot] = make_float4(ta, tb, ra_, rb_);
+        fetch(s0 + 32 + lane);
+        __syncwarp();
+      }
+      const int s1 = min(s0 + 32, npair + 31);
+#pragma unroll 2
+      for (int s = s0; s < s1; ++s) {
+        const int ic = (s - lane) & (kSplatRing - 1);
+        const float Ta = __shfl_up_sync(0xffffffffu, T.x, 1), Tb = __shfl_up_sync(0xffffffffu, T.y, 1);
+        const float Ra = __shfl_up_sync(0xffffffffu, Rr.x, 1), Rb = __shfl_up_sync(0xffffffffu, Rr.y, 1);
+        const float4 q0 = r0[ic], q1 = r1[ic], q2 = r2[ic], q3 = r3[ic];
+        T = lane == 0 ? f2(q3.x, q3.y) : f2(Ta, Tb);
+        Rr = lane == 0 ? f2(q3.z, q3.w) : f2(Ra, Rb);
+        // falloff at both pixels: the forward's operations and roundings
+        const float2 dx = f2_sub(U, f2(q2.x, q2.y)), dy = f2_sub(V, f2(q2.z, q2.w));
+        const float2 tt = f2_fma(BE, dy, dx);
+        const float2 e = f2_fma(f2_mul(A2, tt), tt, f2_mul(G2, f2_mul(dy, dy)));
+        const float2 G = f2(ex2_approx(e.x), ex2_approx(e.y));
+        const float2 raw = f2_mul(O, G);
+        const float2 al = f2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+        // a position before the pixel's stop (false on stopped pixels and for lanes
+        // without an entry) where sigma reaches the floor; elsewhere the pixel gets
+        // sigma 0: T, R and every sum stay as they are
+        const bool oka = jj < __float_as_uint(q1.z) && al.x >= kAlphaMin;
+        const bool okb = jj < __float_as_uint(q1.w) && al.y >= kAlphaMin;
+        const float2 ae = f2(oka ? al.x : 0.f, okb ? al.y : 0.f);
+        const float2 one_m = f2_sub(f2(1.f), ae);
+        const float2 w = f2_mul(ae, T);
+        const float2 gx = f2(q0.x, q0.y), gy = f2(q0.z, q0.w), gz = f2(q1.x, q1.y);
+        const float2 ncd = f2_fma(NCZ, gz, f2_fma(NCY, gy, f2_mul(NCX, gx)));   // -<c, g>
+        Rr = f2_fma(ncd, w, Rr);
+        // -dL/dsigma = -T <c, g> + R / (1 - sigma)
+        const float2 nd = f2_fma(T, ncd, f2_mul(Rr, f2(rcp_approx(one_m.x), rcp_approx(one_m.y))));
+        T = f2_mul(T, one_m);
+        v6 = f2_fma(gx, w, v6);
+        v7 = f2_fma(gy, w, v7);
+        v8 = f2_fma(gz, w, v8);
+        const float2 mg = f2_mul(nd, G);
+        const float2 m = f2(oka && raw.x <= kAlphaMax ? mg.x : 0.f, okb && raw.y <= kAlphaMax ? mg.y : 0.f);
+        const float2 mt = f2_mul(m, tt), mdy = f2_mul(m, dy);
+        v0 = f2_add(v0, mt);
+        v1 = f2_add(v1, mdy);
+        v2 = f2_fma(mt, tt, v2);
+        v3 = f2_fma(mt, dy, v3);
+        v4 = f2_fma(mdy, dy, v4);
+        v5 = f2_add(v5, m);
+      }
+      __syncwarp();   // this chunk's reads before the next chunk's ring writes
+    }
+    const float v[9] = {-(v0.x + v0.y), -(v1.x + v1.y), -(v2.x + v2.y), -(v3.x + v3.y), -(v4.x + v4.y),
+                        -(v5.x + v5.y), v6.x + v6.y, v7.x + v7.y, v8.x + v8.y};
+    if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
+                v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
+      const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
+      red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
+      red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
+      red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
+    }
+    __syncwarp();   // the next bucket rewrites this warp's live list
+    uint32_t nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&s_next, 1u);
+    b = part + kSplatSplit * (int)__shfl_sync(0xffffffffu, nxt, 0);
+  }
+}
+
 __global__ void l1_loss_grad_kernel(const gs_camera_t *__restrict__ cams, const float *__restrict__ image,
                                     const float *__restrict__ target, float *__restrict__ d_image, float *loss) {
   const int v = blockIdx.y;
@@ -754,14 +1037,15 @@ __global__ void l1_loss_grad_kernel(const gs_camera_t *__restrict__ cams, const 
 template <int TW, int TH, bool COUNT = false>
 static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
-                              cudaStream_t s, uint32_t *counts = nullptr, float4 *ckpt = nullptr) {
+                              cudaStream_t s, uint32_t *counts = nullptr, const CkptLayout *ckpt = nullptr) {
   if (!COUNT) {
+    const CkptLayout ck = ckpt ? *ckpt : CkptLayout{};
 #define GS_FWD(CK)                                                                                           \
   raster_fwd_warp_kernel<TW, TH, CK><<<frame->n_tiles, TW * TH / 2, 0, s>>>(                                  \
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),   \
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),  \
       frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,                    \
-      cfg->store_stop ? stop : nullptr, ckpt)
+      cfg->store_stop ? stop : nullptr, ck)
     ckpt ? GS_FWD(true) : GS_FWD(false);
 #undef GS_FWD
     GS_LAUNCH_CHECK();
@@ -807,12 +1091,16 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
 template <int TW, int TH>
 static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
                                     const float *image, const float *d_image, const uint32_t *stop,
-                                    const float4 *ckpt, gs_rec_grads_t *g, cudaStream_t s) {
+                                    const CkptLayout &ckpt, gs_rec_grads_t *g, cudaStream_t s) {
   const size_t R = (size_t)proj->n_records;
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
+#ifdef GS_SPLAT_ONE_PIXEL
   raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
+#else
+  raster_bwd_splat2_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
+#endif
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
@@ -864,10 +1152,57 @@ extern "C" gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bin
   return GS_ERR_UNSUPPORTED;
 }
 
-extern "C" size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity) {
+// Table entries of a frame whose lists hold at most `capacity` entries: one per
+// (bucket, 8 x 8 block); 0 for an unsupported frame.
+static uint64_t ckpt_table_entries(const gs_frame_t *frame, int64_t capacity) {
   if (!frame || capacity < 0 || frame->n_tiles <= 0 || !gs_tile_supported(frame->tile_w, frame->tile_h)) return 0;
   const uint64_t buckets = ((uint64_t)capacity + 31u) / 32u + (uint64_t)frame->n_tiles;
-  return (size_t)(buckets * (uint64_t)frame->tile_w * (uint64_t)frame->tile_h * sizeof(float4));
+  return buckets * (uint64_t)(frame->tile_w * frame->tile_h / 64);
+}
+
+// The largest slot count a buffer of `bytes` holds for this frame and capacity.
+static bool ckpt_from_bytes(const gs_frame_t *frame, int64_t capacity, void *base, size_t bytes, CkptLayout &L) {
+  const uint64_t te = ckpt_table_entries(frame, capacity);
+  if (te == 0) return false;
+  const size_t head = ckpt_layout(nullptr, te, 0).bytes;
+  if (bytes < head) return false;
+  const uint32_t pools = ckpt_pools((uint64_t)frame->n_tiles * (frame->tile_w * frame->tile_h / 64));
+  L = ckpt_layout(base, te, (bytes - head) / (64 * sizeof(float4)), pools);
+  return true;
+}
+
+extern "C" size_t gs_raster_ckpt_size(const gs_frame_t *frame, int64_t capacity, int64_t n_slots) {
+  const uint64_t te = ckpt_table_entries(frame, capacity);
+  if (te == 0) return 0;
+  // a slot for every (bucket, block) pair the lists can have: enough whatever the
+  // stop indices
+  const uint64_t slots = n_slots < 0 ? te : (uint64_t)n_slots;
+  return ckpt_layout(nullptr, te, slots).bytes;
+}
+
+__global__ void ckpt_usage_kernel(const uint32_t *__restrict__ pools, uint32_t n_pools, uint64_t pool_size,
+                                  bool direct, int64_t *out) {
+  // one warp: the slots the last forward needed (n_pools x the fullest pool, the
+  // size at which no pool overflows) and whether any pool overflowed
+  uint32_t mx = 0;
+  for (uint32_t i = threadIdx.x; i < n_pools; i += 32) mx = max(mx, pools[i]);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (threadIdx.x == 0) {
+    out[0] = (int64_t)mx * n_pools;
+    out[1] = (!direct && (uint64_t)mx > pool_size) ? 1 : 0;
+  }
+}
+
+extern "C" gs_status_t gs_raster_ckpt_usage(const gs_frame_t *frame, int64_t capacity, const void *ckpt,
+                                            size_t ckpt_bytes, int64_t *d_usage, gs_stream_t stream) {
+  if (!frame || !ckpt || !d_usage || !a16(ckpt) || (reinterpret_cast<uintptr_t>(d_usage) & 7u) != 0)
+    return GS_ERR_INVALID_ARG;
+  CkptLayout L;
+  if (!ckpt_from_bytes(frame, capacity, const_cast<void *>(ckpt), ckpt_bytes, L)) return GS_ERR_INVALID_ARG;
+  ckpt_usage_kernel<<<1, 32, 0, as_stream(stream)>>>(L.pools, L.n_pools, L.pool_size,
+                                                     L.n_slots >= L.table_entries, d_usage);
+  GS_LAUNCH_CHECK();
+  return GS_OK;
 }
 
 extern "C" gs_status_t gs_raster_fwd_ckpt(const gs_proj_t *proj, const gs_bins_t *bins, const gs_frame_t *frame,
@@ -878,17 +1213,17 @@ extern "C" gs_status_t gs_raster_fwd_ckpt(const gs_proj_t *proj, const gs_bins_t
     return GS_ERR_INVALID_ARG;
   if (!bins->vals || !bins->ranges || !proj->mean2d || !a16(proj->conic_opacity) || !a16(proj->rgb) || !a16(ckpt))
     return GS_ERR_INVALID_ARG;
-  const size_t need = gs_raster_ckpt_size(frame, bins->capacity);
-  if (need == 0) return GS_ERR_UNSUPPORTED;
-  if (ckpt_bytes < need) return GS_ERR_INVALID_ARG;
+  if (!gs_tile_supported(frame->tile_w, frame->tile_h)) return GS_ERR_UNSUPPORTED;
+  CkptLayout L;
+  if (!ckpt_from_bytes(frame, bins->capacity, ckpt, ckpt_bytes, L)) return GS_ERR_INVALID_ARG;
   gs_raster_cfg_t c = *cfg;
   c.store_stop = 1;
   cudaStream_t s = as_stream(stream);
-  float4 *ck = static_cast<float4 *>(ckpt);
-  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_fwd<16, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
-  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_fwd<8, 8>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
-  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_fwd<16, 32>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
-  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_fwd<32, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, ck);
+  GS_CUDA_TRY(cudaMemsetAsync(L.pools, 0, 4 * kCkptPools, s));
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_fwd<16, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, &L);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_fwd<8, 8>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, &L);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_fwd<16, 32>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, &L);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_fwd<32, 16>(proj, bins, frame, &c, image, T_final, stop, s, nullptr, &L);
   return GS_ERR_UNSUPPORTED;
 }
 
@@ -904,15 +1239,14 @@ extern "C" gs_status_t gs_raster_bwd_splat(const gs_proj_t *proj, const gs_bins_
   if (!grads->d_mean2d || !a16(grads->d_conic_opacity) || !a16(grads->d_rgb) || !grads->d_conic_opacity ||
       !grads->d_rgb || ((reinterpret_cast<uintptr_t>(grads->d_mean2d) & 7u) != 0))
     return GS_ERR_INVALID_ARG;
-  const size_t need = gs_raster_ckpt_size(frame, bins->capacity);
-  if (need == 0) return GS_ERR_UNSUPPORTED;
-  if (ckpt_bytes < need) return GS_ERR_INVALID_ARG;
+  if (!gs_tile_supported(frame->tile_w, frame->tile_h)) return GS_ERR_UNSUPPORTED;
+  CkptLayout L;
+  if (!ckpt_from_bytes(frame, bins->capacity, const_cast<void *>(ckpt), ckpt_bytes, L)) return GS_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
-  const float4 *ck = static_cast<const float4 *>(ckpt);
-  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd_splat<16, 16>(proj, bins, frame, image, d_image, stop, ck, grads, s);
-  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd_splat<8, 8>(proj, bins, frame, image, d_image, stop, ck, grads, s);
-  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd_splat<16, 32>(proj, bins, frame, image, d_image, stop, ck, grads, s);
-  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd_splat<32, 16>(proj, bins, frame, image, d_image, stop, ck, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 16) return launch_bwd_splat<16, 16>(proj, bins, frame, image, d_image, stop, L, grads, s);
+  if (frame->tile_w == 8 && frame->tile_h == 8) return launch_bwd_splat<8, 8>(proj, bins, frame, image, d_image, stop, L, grads, s);
+  if (frame->tile_w == 16 && frame->tile_h == 32) return launch_bwd_splat<16, 32>(proj, bins, frame, image, d_image, stop, L, grads, s);
+  if (frame->tile_w == 32 && frame->tile_h == 16) return launch_bwd_splat<32, 16>(proj, bins, frame, image, d_image, stop, L, grads, s);
   return GS_ERR_UNSUPPORTED;
 }
 

@@ -247,18 +247,28 @@ def raster_fwd(proj: Projected, bins: Bins, frame: Frame, bg=(0.0, 0.0, 0.0), st
     return image, T_final, (stop if store_stop else None)
 
 
-def ckpt_bytes(frame: Frame, capacity: int) -> int:
-    """Bytes of the per-splat backward's checkpoint buffer for lists of at most
-    `capacity` entries on this frame."""
-    n = int(lib().gs_raster_ckpt_size(C.byref(frame.frame), int(capacity)))
+def ckpt_bytes(frame: Frame, capacity: int, n_slots: int = -1) -> int:
+    """Bytes of a checkpoint buffer with n_slots 1 KB slots (-1: one for every
+    (bucket, 8x8 block) pair the lists can have, which cannot overflow)."""
+    n = int(lib().gs_raster_ckpt_size(C.byref(frame.frame), int(capacity), int(n_slots)))
     if n == 0:
         raise _abi.GsError(1, f"gs_raster_ckpt_size (frame or capacity {capacity})")
     return n
 
 
-def alloc_ckpt(frame: Frame, bins: "Bins") -> torch.Tensor:
+def alloc_ckpt(frame: Frame, bins: "Bins", n_slots: int = -1) -> torch.Tensor:
     """Checkpoint buffer (uint8, 16-byte aligned) for raster_fwd_ckpt on these bins."""
-    return torch.empty(ckpt_bytes(frame, bins.capacity), dtype=torch.uint8, device=frame.device)
+    return torch.empty(ckpt_bytes(frame, bins.capacity, n_slots), dtype=torch.uint8, device=frame.device)
+
+
+def ckpt_usage(frame: Frame, bins: "Bins", ckpt: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """int64 [2] on the device: (slots the last raster_fwd_ckpt into ckpt needed,
+    1 if it ran out of slots)."""
+    out = torch.empty(2, dtype=torch.int64, device=frame.device) if out is None else out
+    check(lib().gs_raster_ckpt_usage(C.byref(frame.frame), int(bins.capacity), _p(ckpt),
+                                     ckpt.numel() * ckpt.element_size(), _p(out), _stream(stream)),
+          "gs_raster_ckpt_usage")
+    return out
 
 
 def raster_fwd_ckpt(proj: Projected, bins: Bins, frame: Frame, ckpt: torch.Tensor, bg=(0.0, 0.0, 0.0),
@@ -364,43 +374,67 @@ def densify_cfg(mode=DENSIFY_ADAPTIVE, grad_threshold=2e-4, log_scale_threshold=
     return c
 
 
-def densify_select(cfg: _abi.GsDensifyCfg, params: dict, accum, count, ws=None, stream=None):
+def densify_select(cfg: _abi.GsDensifyCfg, params: dict, accum, count, ws=None, stream=None, out=None):
+    """out: optional preallocated (split, clone, tau, new_n)."""
     n = params["means"].shape[0]
     dev = params["means"].device
     ws = _bytes(lib().gs_densify_workspace_size(n), dev) if ws is None else ws
-    split = torch.empty(n, dtype=torch.uint8, device=dev)
-    clone = torch.empty(n, dtype=torch.uint8, device=dev)
-    tau = torch.empty(1, dtype=torch.float32, device=dev)
-    new_n = torch.empty(1, dtype=torch.int64, device=dev)
+    if out is None:
+        split = torch.empty(n, dtype=torch.uint8, device=dev)
+        clone = torch.empty(n, dtype=torch.uint8, device=dev)
+        tau = torch.empty(1, dtype=torch.float32, device=dev)
+        new_n = torch.empty(1, dtype=torch.int64, device=dev)
+    else:
+        split, clone, tau, new_n = out
     check(lib().gs_densify_select(C.byref(cfg), _p(params["log_scales"]), _p(params["opacity_logits"]),
                                   _p(accum), _p(count), n, _p(split), _p(clone), _p(tau), _p(new_n), _p(ws),
                                   ws.numel(), _stream(stream)), "gs_densify_select")
     return split, clone, tau, new_n, ws
 
 
+PROV_KEYS = ("origin", "splits", "clones")
+
+
 def densify_apply(cfg: _abi.GsDensifyCfg, params: dict, sh_degree: int, split, clone, tau, capacity: int,
-                  extra: Optional[dict] = None, ws=None, stream=None):
+                  extra: Optional[dict] = None, ws=None, stream=None, out=None, ex_out=None, new_n=None,
+                  err=None, prov: Optional[dict] = None):
+    """out / ex_out / new_n / err: optional preallocated outputs (capacity rows).
+    prov: optional provenance {origin, splits, clones} (int32 [n]); their outputs
+    (int32 [capacity]) are returned in out under the same keys."""
     ps = params_struct(params, sh_degree)
     dev = params["means"].device
     ws = _bytes(lib().gs_densify_workspace_size(ps.n), dev) if ws is None else ws
-    out = {k: torch.empty((capacity,) + tuple(params[k].shape[1:]), dtype=torch.float32, device=dev)
-           for k in PARAM_KEYS}
+    if out is None:
+        out = {k: torch.empty((capacity,) + tuple(params[k].shape[1:]), dtype=torch.float32, device=dev)
+               for k in PARAM_KEYS}
     po = _abi.GsParamsOut()
     po.means, po.log_scales, po.quats = out["means"].data_ptr(), out["log_scales"].data_ptr(), out["quats"].data_ptr()
     po.opacity_logits, po.sh = out["opacity_logits"].data_ptr(), out["sh"].data_ptr()
     extra = extra or {}
-    ex_out = {}
+    given = ex_out is not None
+    ex_out = dict(ex_out) if given else {}
     arr = (_abi.GsExtraArray * max(1, len(extra)))()
     for i, (k, src) in enumerate(extra.items()):
         src = _need(src, torch.float32, k)
-        dst = torch.empty((capacity,) + tuple(src.shape[1:]), dtype=torch.float32, device=dev)
+        dst = ex_out[k] if given else torch.empty((capacity,) + tuple(src.shape[1:]), dtype=torch.float32, device=dev)
         ex_out[k] = dst
         arr[i].src, arr[i].dst, arr[i].width = src.data_ptr(), dst.data_ptr(), int(src[0].numel()) if src.shape[0] else 1
-    new_n = torch.empty(1, dtype=torch.int64, device=dev)
-    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    new_n = torch.empty(1, dtype=torch.int64, device=dev) if new_n is None else new_n
+    err = torch.zeros(1, dtype=torch.int32, device=dev) if err is None else err
+    pv = None
+    if prov is not None:
+        pv = _abi.GsProvenance()
+        for k in PROV_KEYS:
+            src = _need(prov[k], torch.int32, k)
+            dst = out.get(k)
+            if dst is None:
+                dst = torch.empty(capacity, dtype=torch.int32, device=dev)
+                out[k] = dst
+            setattr(pv, f"{k}_in", src.data_ptr())
+            setattr(pv, f"{k}_out", dst.data_ptr())
     check(lib().gs_densify_apply(C.byref(cfg), C.byref(ps), _p(split), _p(clone), _p(tau), C.byref(po), arr,
-                                 len(extra), int(capacity), _p(new_n), _p(err), _p(ws), ws.numel(),
-                                 _stream(stream)), "gs_densify_apply")
+                                 len(extra), C.byref(pv) if pv is not None else None, int(capacity), _p(new_n),
+                                 _p(err), _p(ws), ws.numel(), _stream(stream)), "gs_densify_apply")
     return out, ex_out, new_n, err
 
 

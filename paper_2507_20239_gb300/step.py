@@ -10,8 +10,10 @@ backward recomputes the cut-off (4 bytes per pixel less). No count returns to th
 the sequence can be captured once into a CUDA graph (capture()) and replayed.
 
 The duplicate capacity of the per-tile lists is sized from a measured M with
-headroom; gs_bin_sort raises its device error word if a later view exceeds it
-(check error() outside any graph).
+headroom, and the per-splat forward's checkpoint slots from a measured count with
+the same headroom; gs_bin_sort raises its device error word if a later view exceeds
+the capacity, and error() also reports a forward that ran out of checkpoint slots
+(check it outside any graph).
 """
 from __future__ import annotations
 
@@ -57,9 +59,20 @@ def duplicates(params: dict, sh_degree: int, frame: R.Frame) -> int:
     return int(bins.count.item())
 
 
+def ckpt_slots(params: dict, sh_degree: int, frame: R.Frame, capacity: int) -> int:
+    """Checkpoint slots the per-splat forward needs for these parameters on this frame
+    (one projection, binning and forward into a buffer without slots, synchronising)."""
+    proj = R.project(params, sh_degree, frame)
+    bins = R.bin_sort(proj, frame, capacity=capacity)
+    ck = R.alloc_ckpt(frame, bins, 0)
+    R.raster_fwd_ckpt(proj, bins, frame, ck)
+    return int(R.ckpt_usage(frame, bins, ck)[0].item())
+
+
 class TrainStep:
     def __init__(self, params: dict, sh_degree: int, cameras, target_images, config: StepConfig = StepConfig(),
-                 device="cuda", capacity: int | None = None, headroom: float = 1.25, store_stop: bool = True):
+                 device="cuda", capacity: int | None = None, headroom: float = 1.25, store_stop: bool = True,
+                 slots: int | None = None):
         self.P, self.sh_degree, self.config = params, int(sh_degree), config
         self.splat = config.backward == "splat"
         self.store_stop = bool(store_stop) or self.splat   # the per-splat backward needs the stop indices
@@ -74,7 +87,14 @@ class TrainStep:
         self.image = torch.empty(3 * f.n_pixels, device=f.device)
         self.T = torch.empty(f.n_pixels, device=f.device)
         self.stop = torch.empty(f.n_pixels, dtype=torch.int32, device=f.device) if self.store_stop else None
-        self.ckpt = R.alloc_ckpt(f, self.bins) if self.splat else None
+        self.ckpt = None
+        if self.splat:
+            # checkpoint slots for the (bucket, block) pairs the forward walks, measured
+            # with headroom (-1: one per possible pair)
+            if slots is None:
+                slots = int(ckpt_slots(params, sh_degree, f, capacity) * headroom) + 4 * 256
+            self.ckpt = R.alloc_ckpt(f, self.bins, slots)
+            self.ckpt_use = torch.zeros(2, dtype=torch.int64, device=f.device)
         self.d_image = torch.empty_like(self.image)
         self.loss = torch.empty(f.n_views, device=f.device)
         self.target = f.pack_images(target_images).contiguous()
@@ -127,5 +147,18 @@ class TrainStep:
         return g
 
     def error(self) -> int:
-        """gs_bin_sort's device error word (0: every list fitted the capacity)."""
-        return int(self.bins.error.item())
+        """gs_bin_sort's device error word (0: every list fitted the capacity), with
+        GS_ERR_CAPACITY also set when the per-splat forward ran out of checkpoint slots."""
+        err = int(self.bins.error.item())
+        if self.ckpt is not None:
+            R.ckpt_usage(self.frame, self.bins, self.ckpt, out=self.ckpt_use)
+            if int(self.ckpt_use[1].item()):
+                err |= 2
+        return err
+
+    def memory_bytes(self) -> dict:
+        """Device bytes of the step's largest buffers."""
+        nb = lambda t: 0 if t is None else t.numel() * t.element_size()
+        return {"bins": nb(self.bins.vals) + nb(self.bins.ws) + nb(self.bins.keys), "ckpt": nb(self.ckpt),
+                "records": sum(nb(getattr(self.proj, k)) for k in ("mean2d", "conic_opacity", "rgb", "depth",
+                                                                     "radius", "rect", "clamped"))}

@@ -280,6 +280,30 @@ def large_scene(seed: int = 4, n: int = 5_000_000, n_views: int = 4, width=1600,
     return sc
 
 
+def sfm_like_init(gt: Scene, n: int, seed: int = 3, jitter: float = 0.01, sh_degree: int = 3,
+                  colour_noise: float = 0.1) -> Scene:
+    """An initial scene of the kind a structure-from-motion point cloud gives the 3DGS
+    lineage, drawn from a ground-truth scene instead of from its generator: n of its
+    means (without replacement) jittered by N(0, jitter^2) per axis, the colour of the
+    picked Gaussian (its DC coefficient plus N(0, colour_noise^2)), isotropic
+    log-scales log(mean distance to the 3 nearest picked points), identity
+    rotations, opacity 0.1 and zero higher SH bands."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(gt.n, n, replace=False)
+    means = gt.means[idx].astype(np.float64) + rng.normal(0.0, jitter, (n, 3))
+    d, _ = cKDTree(means).query(means, k=4)
+    scale = np.maximum(d[:, 1:].mean(1), 1e-7)
+    log_scales = np.repeat(np.log(scale)[:, None], 3, 1)
+    quats = np.zeros((n, 4))
+    quats[:, 0] = 1.0
+    logits = np.full(n, math.log(0.1 / 0.9))
+    sh = np.zeros((n, (sh_degree + 1) ** 2, 3))
+    sh[:, 0, :] = gt.sh[idx, 0, :] + rng.normal(0.0, colour_noise, (n, 3))
+    m, s, q, o, c = _f32(means, log_scales, quats, logits, sh)
+    return Scene(m, s, q, o, c, sh_degree, name=f"sfm-init-{n}")
+
+
 def random_records(seed: int, n: int, width: int, height: int, max_radius: int = 40,
                    cull_frac: float = 0.1):
     """Synthetic projected records (mean2d, depth, radius) for testing binning

@@ -89,6 +89,12 @@ class Trainer:
         self.event = 0
         self._set_params({k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).to(device)
                           for k, v in params.items()}, None)
+        # provenance of every Gaussian: its ancestor in the initial set and the
+        # splits and clones on its lineage (carried through gs_densify_apply)
+        n0 = self.n
+        self.prov = {"origin": torch.arange(n0, dtype=torch.int32, device=self.device),
+                     "splits": torch.zeros(n0, dtype=torch.int32, device=self.device),
+                     "clones": torch.zeros(n0, dtype=torch.int32, device=self.device)}
 
     # ---------------------------------------------------------------- state
     def _set_params(self, tensors: dict, moments: Optional[dict], step=0):
@@ -152,7 +158,7 @@ class Trainer:
         step = self.opt.t
         cap = int(new_n.item())
         out, ex, got_n, err = R.densify_apply(cfg, P, self.sh_degree(it), split, clone, tau, cap, extra=extra,
-                                              ws=ws)
+                                              ws=ws, prov=self.prov)
         if int(err.item()) != 0 or int(got_n.item()) != cap:
             raise RuntimeError("densify: output capacity")
         if self.on_densify is not None:
@@ -160,10 +166,25 @@ class Trainer:
                                  prune_ratio=self.sched.prune_ratio, prune_upper_tau=self.sched.prune_upper_tau,
                                  params=P, accum=self.stats.accum, count=self.stats.count, extra=extra,
                                  split=split, clone=clone, tau=tau, out=out, out_extra=ex, seed=self.sched.seed,
-                                 event=self.event))
+                                 event=self.event, prov=self.prov))
         self.events.append((it, int(mode), int(split.sum().item()), int(clone.sum().item()), self.n, cap))
         self.event += 1
+        self.prov = {k: out.pop(k) for k in R.PROV_KEYS}
         self._set_params(out, ex, step)
+
+    def provenance_summary(self) -> dict:
+        """Shares of the current Gaussians by lineage (the split/clone analysis of
+        Sec. "Global-to-local framework"): untouched initial Gaussians, those with a
+        clone, with a split, with both, and the initial Gaussians with descendants."""
+        s, c = self.prov["splits"], self.prov["clones"]
+        n = max(1, self.n)
+        return {"n": self.n, "untouched": float(((s == 0) & (c == 0)).sum()) / n,
+                "with_clone": float(((c > 0) & (s == 0)).sum()) / n,
+                "with_split": float(((s > 0) & (c == 0)).sum()) / n,
+                "with_both": float(((s > 0) & (c > 0)).sum()) / n,
+                "max_splits": int(s.max().item()) if self.n else 0,
+                "max_clones": int(c.max().item()) if self.n else 0,
+                "origins_alive": int(torch.unique(self.prov["origin"]).numel())}
 
     def run(self, log_every: int = 100):
         for it in range(1, self.sched.total + 1):
@@ -246,6 +267,9 @@ def main(argv=None):
     ap.add_argument("--views", type=int, default=8)
     ap.add_argument("--init-log-scale", type=float, default=-4.0,
                     help="mean log-scale of the initial Gaussians (the generator's default: -4)")
+    ap.add_argument("--init-mode", choices=["generator", "sfm"], default="generator",
+                    help="initial Gaussians: a fresh draw of the scene generator (seed 3), or an "
+                         "SfM-like point set taken from the ground truth (synth.sfm_like_init)")
     ap.add_argument("--grad-threshold", type=float, default=2e-4)
     ap.add_argument("--energy", type=int, default=0, metavar="K",
                     help="derive the stages from the targets' energy schedule with scales 1..K "
@@ -274,13 +298,17 @@ def main(argv=None):
     else:
         cams = orbit_views(args.views, args.width, args.height, float(args.width))
         views = {r: (c, render_targets(gt.params(), 3, c)) for r, c in cams.items()}
-    init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
+    if args.init_mode == "sfm":
+        init = synth.sfm_like_init(gt, args.init, seed=3).params()
+    else:
+        init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
     tr = Trainer(init, views, sched, extent=1.1 * 4.0)
     hist = tr.run()
     n_split = sum(e[2] for e in tr.events)
     n_clone = sum(e[3] for e in tr.events)
     print(json.dumps({"history": hist, "final_n": tr.n, "events": tr.events,
                       "new_from_clone": n_clone / max(1, n_clone + 2 * n_split), "init_log_scale": args.init_log_scale,
+                      "init_mode": args.init_mode, "provenance": tr.provenance_summary(),
                       "grad_threshold": args.grad_threshold, "prune_ratio": args.prune_ratio,
                       "prune_upper": args.prune_upper, "energy_schedule": energy}))
 

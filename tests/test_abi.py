@@ -52,6 +52,7 @@ STRUCTS = {
     "gs_densify_cfg_t": (_abi.GsDensifyCfg, ["mode", "prune_upper_logit", "prune_ratio", "seed", "event"]),
     "gs_extra_array_t": (_abi.GsExtraArray, ["src", "dst", "width"]),
     "gs_params_out_t": (_abi.GsParamsOut, ["means", "sh"]),
+    "gs_provenance_t": (_abi.GsProvenance, ["origin_in", "clones_in", "origin_out", "clones_out"]),
 }
 
 
@@ -114,10 +115,16 @@ def test_host_argument_checks_return_invalid_arg(lib):
     assert lib.gs_project(C.byref(p), C.byref(fr), None, None) == 1
 
 
+def _a256(x):
+    return (x + 255) // 256 * 256
+
+
 def test_checkpoint_size_and_bucket_layout(lib):
-    """gs_raster_ckpt_size's formula, and the bucket numbering it relies on: tile t's
-    32-entry buckets b are floor(s_t / 32) + t + b for a list starting at s_t, which
-    never overlap between tiles and stay below ceil(M / 32) + n_tiles."""
+    """gs_raster_ckpt_size's formula (256 pool counters, a 4-byte table entry per
+    (bucket, 8x8 block), 1 KB per slot; n_slots < 0: a slot per table entry), and the
+    bucket numbering it relies on: tile t's 32-entry buckets b are floor(s_t / 32) +
+    t + b for a list starting at s_t, which never overlap between tiles and stay below
+    ceil(M / 32) + n_tiles."""
     import numpy as np
     cams = (_abi.GsCamera * 2)()
     for i, (w, h) in enumerate([(623, 413), (1246, 826)]):
@@ -128,9 +135,14 @@ def test_checkpoint_size_and_bucket_layout(lib):
         fr = _abi.GsFrame()
         assert lib.gs_frame_init(cams, 2, tw, th, C.byref(fr)) == 0
         for cap in (0, 1, 31, 32, 33, 1_000_003):
-            assert lib.gs_raster_ckpt_size(C.byref(fr), cap) == ((cap + 31) // 32 + fr.n_tiles) * tw * th * 16
-        assert lib.gs_raster_ckpt_size(C.byref(fr), -1) == 0
-    assert lib.gs_raster_ckpt_size(None, 10) == 0
+            entries = ((cap + 31) // 32 + fr.n_tiles) * (tw * th // 64)
+            head = 1024 + _a256(4 * entries)
+            assert lib.gs_raster_ckpt_size(C.byref(fr), cap, 0) == head
+            assert lib.gs_raster_ckpt_size(C.byref(fr), cap, 1000) == head + 1000 * 1024
+            assert lib.gs_raster_ckpt_size(C.byref(fr), cap, -1) == head + entries * 1024
+        assert lib.gs_raster_ckpt_size(C.byref(fr), -1, 0) == 0
+    assert lib.gs_raster_ckpt_size(None, 10, 0) == 0
+    assert lib.gs_raster_ckpt_usage(None, 0, None, 0, None, None) == 1
     assert lib.gs_raster_fwd_ckpt(None, None, None, None, None, None, None, None, 0, None) == 1
     assert lib.gs_raster_bwd_splat(None, None, None, None, None, None, None, 0, None, None) == 1
     rng = np.random.default_rng(0)

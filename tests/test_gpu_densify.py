@@ -86,14 +86,20 @@ def test_densify_apply_bit_exact(adaptive):
                                                     torch.as_tensor(count).cuda())
     rng = np.random.default_rng(9)
     m1 = rng.normal(size=(n, 3)).astype(np.float32)
+    # provenance from an earlier event: origins and counts of an arbitrary lineage
+    prov = dict(origin=rng.integers(0, 10 * n, n).astype(np.int32), splits=rng.integers(0, 4, n).astype(np.int32),
+                clones=rng.integers(0, 3, n).astype(np.int32))
     cap = int(new_n.item())
     out, ex, got_n, err = R.densify_apply(cfg, P, 1, split, clone, tau, cap, extra={"m1": torch.as_tensor(m1).cuda()},
-                                          ws=ws)
+                                          ws=ws, prov={k: torch.as_tensor(v).cuda() for k, v in prov.items()})
     torch.cuda.synchronize()
     assert int(err.item()) == 0 and int(got_n.item()) == cap
     ws_, wc = oden.select(accum, count, p["log_scales"], 0, np.float32(2e-4), thr_s)
-    want, wex, idx = oden.apply(p, ws_, wc, np.float32(tau.item()), 1234567, 7, extra={"m1": m1})
+    want, wex, idx = oden.apply(p, ws_, wc, np.float32(tau.item()), 1234567, 7, extra={"m1": m1},
+                                provenance=prov)
     assert cap == len(idx["source"])
+    for k in R.PROV_KEYS:
+        assert np.array_equal(out[k].cpu().numpy(), idx["provenance"][k]), k
     for k in ("log_scales", "quats", "opacity_logits", "sh"):
         assert np.array_equal(out[k].cpu().numpy(), want[k]), k
     assert np.array_equal(ex["m1"].cpu().numpy(), wex["m1"])

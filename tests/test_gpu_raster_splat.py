@@ -178,9 +178,11 @@ def test_ckpt_size_and_argument_errors():
     rec = oracle_records_fp32(sc.params(), sc.sh_degree, cam)
     frame, proj, bins, img, stop, ckpt = _fwd_both([rec], [cam], (16, 16), (0, 0, 0))
     cap = bins.capacity
-    assert R.ckpt_bytes(frame, cap) == ((cap + 31) // 32 + frame.n_tiles) * 256 * 16
+    entries = ((cap + 31) // 32 + frame.n_tiles) * 4
+    head = 1024 + (4 * entries + 255) // 256 * 256
+    assert R.ckpt_bytes(frame, cap) == head + entries * 1024
     assert ckpt.numel() == R.ckpt_bytes(frame, cap)
-    short = ckpt[:ckpt.numel() - 16]
+    short = ckpt[:head - 16]                       # not even the pool counters and table
     with pytest.raises(GsError):
         R.raster_fwd_ckpt(proj, bins, frame, short)
     dg = torch.zeros_like(img)
@@ -190,6 +192,42 @@ def test_ckpt_size_and_argument_errors():
         R.raster_bwd_splat(proj, bins, frame, img, dg, stop, ckpt[8:])      # not 16-byte aligned
     with pytest.raises(GsError):
         R.ckpt_bytes(frame, -1)
+
+
+@pytest.mark.parametrize("name,tile", [("orbit_small", (16, 16)), ("orbit_small", (32, 16)), ("orbit", (16, 16))])
+def test_measured_checkpoint_slots(name, tile):
+    """A buffer sized from the measured slot count (a forward into a buffer without
+    slots reports it) gives the gradients of the buffer with a slot for every
+    (bucket, block) pair; a buffer with too few slots reports it and runs without
+    fault."""
+    sc = scene(name)
+    cam = sc.cameras[0]
+    frame = R.Frame([cam], tile=tile)
+    proj = R.project({k: torch.as_tensor(v).cuda() for k, v in sc.params().items()}, sc.sh_degree, frame)
+    bins = R.bin_sort(proj, frame)
+    probe = R.alloc_ckpt(frame, bins, 0)
+    R.raster_fwd_ckpt(proj, bins, frame, probe)
+    use = R.ckpt_usage(frame, bins, probe).cpu().numpy()
+    need = int(use[0])
+    assert need > 0 and use[1] == 1
+    full = R.alloc_ckpt(frame, bins)
+    fit = R.alloc_ckpt(frame, bins, need)
+    dg = torch.as_tensor(np.random.default_rng(2).normal(0, 1, 3 * frame.n_pixels).astype(np.float32)).cuda()
+    grads = {}
+    for label, ck in (("full", full), ("fit", fit)):
+        img, T, stop = R.raster_fwd_ckpt(proj, bins, frame, ck)
+        assert int(R.ckpt_usage(frame, bins, ck)[1].item()) == 0
+        grads[label] = _grads(R.raster_bwd_splat(proj, bins, frame, img, dg, stop, ck))
+    for k in grads["full"]:
+        assert rel_l2(grads["fit"][k], grads["full"][k]) < 1e-5, k
+    print(f"{name} {tile}: {need} slots, {fit.numel() / 1e6:.1f} MB against {full.numel() / 1e6:.1f} MB")
+    assert fit.numel() < (0.2 if name == "orbit" else 0.8) * full.numel()
+    small = R.alloc_ckpt(frame, bins, need // 2)
+    img, T, stop = R.raster_fwd_ckpt(proj, bins, frame, small)
+    assert int(R.ckpt_usage(frame, bins, small)[1].item()) == 1
+    g = _grads(R.raster_bwd_splat(proj, bins, frame, img, dg, stop, small))
+    torch.cuda.synchronize()
+    assert all(np.isfinite(v).all() for v in g.values())
 
 
 def test_autograd_splat_backward_matches_pixel_backward():

@@ -35,8 +35,11 @@ def _checker(events, adaptive):
             tau = oden.prune_threshold(p["opacity_logits"], ws_, wc, fixed_tau=0.005)
         assert np.float32(ev["tau"].item()) == tau
         extra = {k: np_(v) for k, v in ev["extra"].items()}
-        want, wex, idx = oden.apply(p, ws_, wc, tau, ev["seed"], ev["event"], extra=extra)
+        prov = {k: np_(v) for k, v in ev["prov"].items()}
+        want, wex, idx = oden.apply(p, ws_, wc, tau, ev["seed"], ev["event"], extra=extra, provenance=prov)
         out = {k: np_(v) for k, v in ev["out"].items()}
+        for k in R.PROV_KEYS:
+            assert np.array_equal(out[k], idx["provenance"][k]), k
         assert out["means"].shape[0] == len(idx["source"])
         for k in ("log_scales", "quats", "opacity_logits", "sh"):
             assert np.array_equal(out[k], want[k]), k

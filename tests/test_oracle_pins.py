@@ -812,3 +812,42 @@ def test_fp32_band_lists_hold_every_exact_pair():
     listed, must, between = exact_list_check(rec["mean2d"], rec["conic_f"], rec["q_max"], rec["radius"],
                                              cam.width, cam.height, (16, 16), tiles, recs)
     assert listed > 50_000 and must > 0.99 * listed and between < 1e-3 * listed
+
+
+def test_provenance_follows_lineage_simulation():
+    # two densification events on a tiny set, tracked as a plain object lineage
+    # (each Gaussian a record (origin, splits, clones); a split makes two children
+    # and removes the parent, a clone adds a copy, a Gaussian whose logit is below
+    # tau is dropped with everything it would produce) against the oracle's arrays
+    rng = np.random.default_rng(17)
+    n = 40
+    params = dict(means=rng.normal(size=(n, 3)).astype(np.float32),
+                  log_scales=rng.normal(-3, 0.3, (n, 3)).astype(np.float32),
+                  quats=rng.normal(size=(n, 4)).astype(np.float32),
+                  opacity_logits=rng.normal(size=n).astype(np.float32),
+                  sh=rng.normal(size=(n, 1, 3)).astype(np.float32))
+    prov = dict(origin=np.arange(n, dtype=np.int32), splits=np.zeros(n, np.int32), clones=np.zeros(n, np.int32))
+    lineage = [(g, 0, 0) for g in range(n)]
+    tau = np.float32(-1.0)
+    for event in range(2):
+        m = params["means"].shape[0]
+        split = rng.uniform(size=m) < 0.2
+        clone = ~split & (rng.uniform(size=m) < 0.2)
+        logits = params["opacity_logits"].copy()
+        params, _, idx = oden.apply(params, split, clone, tau, seed=5, event=event, provenance=prov)
+        prov = idx["provenance"]
+        surv, clones, children = [], [], []
+        for i, (o, sp, cl) in enumerate(lineage):
+            if logits[i] < tau:
+                continue
+            if split[i]:
+                children += [(o, sp + 1, cl), (o, sp + 1, cl)]
+            else:
+                surv.append((o, sp, cl))
+                if clone[i]:
+                    clones.append((o, sp, cl + 1))
+        lineage = surv + clones + children
+        got = list(zip(prov["origin"].tolist(), prov["splits"].tolist(), prov["clones"].tolist()))
+        assert got == lineage
+        assert params["means"].shape[0] == len(lineage)
+    assert any(sp == 2 for _, sp, _ in lineage) or any(cl >= 1 and sp >= 1 for _, sp, cl in lineage)
