@@ -207,19 +207,25 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     co_n = conic_o[r_next];
     c_n = rgb[r_next];
   }
+  // checkpoint slot claims (lane 0): the pool of this (tile, block), and the claim for
+  // the first step
+  const uint32_t pool = CKPT ? (((uint32_t)tile * NW + warp) & (ckpt.n_pools - 1)) : 0u;
+  uint32_t claim = 0;
+  if (CKPT && lane == 0 && n > 0) claim = atomicAdd(ckpt.pools + pool, 1u);
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
     if (CKPT) {
       // state before list position base: (T, accumulated colour) for the per-splat
-      // backward, in a slot this warp claims for (bucket, its 8 x 8 block)
+      // backward, in the slot claimed for (bucket, this warp's 8 x 8 block); the claim
+      // for the next step is issued now and its result used a step later, so the
+      // atomic's round trip overlaps the compositing
       uint32_t slot = kCkptNone;
       if (lane == 0) {
         const uint64_t idx = (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * NW + warp;
-        const uint32_t pool = ((uint32_t)tile * NW + warp) & (ckpt.n_pools - 1);
-        const uint32_t k = atomicAdd(ckpt.pools + pool, 1u);
         if (ckpt.n_slots >= ckpt.table_entries) slot = (uint32_t)idx;      // room for every pair
-        else if (k < ckpt.pool_size) slot = (uint32_t)(pool * ckpt.pool_size + k);
+        else if (claim < ckpt.pool_size) slot = (uint32_t)(pool * ckpt.pool_size + claim);
         ckpt.table[idx] = slot;
+        if (base + 32 < n) claim = atomicAdd(ckpt.pools + pool, 1u);
       }
       slot = __shfl_sync(0xffffffffu, slot, 0);
       if (slot != kCkptNone) {
@@ -606,190 +612,25 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
 // tile's CTAs claim its 32-entry buckets (up to the tile's largest stop index) one
 // at a time, one entry per lane. A bucket's live pixels (stop index beyond its
 // first position) start from the forward's checkpoint (T and the colour composited
-// before the bucket) and flow through the warp diagonally: at step s lane l works on
-// live pixel s - l, taking (T, R) from lane l - 1, which handled that pixel one step
-// earlier, in list order. A tile's buckets are shared by kSplatSplit CTAs, so a tile
-// with a long list does not hold the end of the launch. Each lane sums its entry's
-// moments over the tile's pixels in registers and adds them to the record gradients
-// once, with no cross-lane reduction. Since the lanes only ever read 32 consecutive
-// live pixels, a warp keeps them in a 64-slot ring refilled every 32 steps (the next
-// 32 pixels' checkpoints are loaded meanwhile), which keeps shared memory per CTA
-// small and occupancy high.
-// Needs the stop indices and the checkpoints written by the forward
+// before the bucket), taken in pairs (2 i, 2 i + 1), and the pairs flow through the
+// warp diagonally: at step s lane l works on pair s - l, taking both pixels' (T, R)
+// from lane l - 1, which handled that pair one step earlier, in list order. The two
+// pixels are independent, so every FP32 operation of a step is a packed pair
+// (add/sub/mul/fma.rn.f32x2), which halves the issue slots of the per-pixel chain.
+// A tile's buckets are shared by kSplatSplit CTAs, so a tile with a long list does
+// not hold the end of the launch. Each lane sums its entry's moments over the tile's
+// pixels in registers and adds them to the record gradients once, with no cross-lane
+// reduction. Since the lanes only ever read 32 consecutive pairs, a warp keeps them
+// in a 64-slot ring refilled every 32 steps (the next 32 pairs' checkpoints are
+// loaded meanwhile); the ring holds each pair interleaved, (a, b) in adjacent lanes of
+// each float4, so the shared-memory loads deliver packed operands directly. A
+// pixel's falloff, floor and stop decisions are the forward's own (same operations,
+// same roundings). Needs the stop indices and the checkpoints written by the forward
 // (gs_raster_fwd_ckpt).
 constexpr int kSplatThreads = 128;
 constexpr int kSplatSplit = 2;     // CTAs per tile (bucket b goes to CTA b % kSplatSplit)
 constexpr int kSplatRing = 64;
-
-template <int TW, int TH>
-__global__ void __launch_bounds__(kSplatThreads, 9) raster_bwd_splat_kernel(
-    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
-    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
-    int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
-    const uint32_t *__restrict__ stop_in, const CkptLayout ckpt, float *__restrict__ g_mean2d,
-    float *__restrict__ g_co, float *__restrict__ g_rgb) {
-  constexpr int NP = TW * TH, NW = kSplatThreads / 32, NB = TW * TH / 64;
-  static_assert(NP % 32 == 0 && NP <= 65536, "whole warps of pixels, 16-bit indices");
-  __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
-  __shared__ uint32_t s_stop[NP];
-  __shared__ uint16_t s_live[NW][NP];              // the bucket's live pixels, in pixel order
-  __shared__ float4 s_ra[NW][kSplatRing];          // ring: (dL/dout, stop bits) of live pixel i at i % 64
-  __shared__ float4 s_rb[NW][kSplatRing];          // ring: (x, y, T, R) at the bucket start
-  __shared__ uint32_t s_max, s_next;
-  const int tile = blockIdx.x / kSplatSplit, part = blockIdx.x % kSplatSplit;
-  const TileCoord tc = tile_coord(cams, n_views, tile);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  if (t == 0) {
-    s_max = 0;
-    s_next = NW;
-  }
-  __syncthreads();
-  {
-    const int64_t plane = (int64_t)tc.W * tc.H;
-    const float *img = image + 3 * tc.pix_off;
-    const float *dim = d_image + 3 * tc.pix_off;
-    uint32_t mx = 0;
-    for (int p = t; p < NP; p += kSplatThreads) {
-      const int px = tc.tx * TW + p % TW, py = tc.ty * TH + p / TW;
-      uint32_t st = 0;
-      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (px < tc.W && py < tc.H) {
-        const int64_t q = (int64_t)py * tc.W + px;
-        st = stop_in[tc.pix_off + q];
-        g.x = dim[q]; g.y = dim[plane + q]; g.z = dim[2 * plane + q];
-        g.w = g.x * img[q] + g.y * img[plane + q] + g.z * img[2 * plane + q];
-      }
-      s_g[p] = g;
-      s_stop[p] = st;
-      mx = max(mx, st);
-    }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0) atomicMax(&s_max, mx);
-  }
-  __syncthreads();
-  const uint2 rg = ranges[tile];
-  const int n = min((int)(rg.y - rg.x), (int)s_max);
-  const int nb = (n + 31) >> 5;
-  const uint64_t bk0 = ckpt_bucket(rg.x, tile);
-  uint16_t *live = s_live[warp];
-  float4 *ra = s_ra[warp], *rb = s_rb[warp];
-  // this CTA's buckets b = part + kSplatSplit c: c = warp first, then the next
-  // unclaimed one (earlier buckets hold more live pixels, so a fixed round robin
-  // would load the warps unevenly)
-  for (int b = part + kSplatSplit * warp; b < nb;) {
-    const int j = 32 * b + lane;   // this lane's list position
-    const bool has = j < n;
-    uint32_t r = 0;
-    float2 xy = make_float2(0.f, 0.f);
-    float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cu = co, c = co;
-    if (has) {
-      r = vals[rg.x + j];
-      xy = mean2d[r];
-      cu = conic_o[r];
-      c = rgb[r];
-      co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
-    }
-    int nl = 0;
-    for (int p0 = 0; p0 < NP; p0 += 32) {
-      const int p = p0 + lane;
-      const bool on = s_stop[p] > (uint32_t)(32 * b);
-      const uint32_t bal = __ballot_sync(0xffffffffu, on);
-      if (on) live[nl + __popc(bal & lt)] = (uint16_t)p;
-      nl += __popc(bal);
-    }
-    __syncwarp();
-    // the slot of each 8 x 8 block at this bucket (lane k holds block k's); a block
-    // holding a live pixel was walked by its forward warp, so its entry is current
-    uint32_t bslot = kCkptNone;
-    if (lane < NB) bslot = ckpt.table[(bk0 + (uint64_t)b) * NB + lane];
-    // live pixel `slot` for this lane: its index (-1 past the list) and checkpoint
-    int pn = -1;
-    float4 kn = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto fetch = [&](int slot) {
-      pn = slot < nl ? (int)live[slot] : -1;
-      const int px = pn & (TW - 1), py = pn / TW;
-      const uint32_t sl = __shfl_sync(0xffffffffu, bslot, (py >> 3) * (TW / 8) + (px >> 3));
-      kn = make_float4(1.f, 0.f, 0.f, 0.f);
-      if (pn >= 0 && sl != kCkptNone) kn = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
-    };
-    fetch(lane);
-    // ring slots 32..63 read as stopped until the second chunk replaces them: lanes
-    // whose pixel index is still negative (i & 63 in 33..63) need no bounds test
-    ra[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    rb[32 + lane] = make_float4(0.f, 0.f, 1.f, 0.f);
-    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float T = 1.f, Rr = 0.f;
-    const uint32_t jj = (uint32_t)j;
-    for (int s0 = 0; s0 < nl + 31; s0 += 32) {
-      {
-        // ring slots s0 .. s0 + 31 (those of s0 - 64 .. s0 - 33 are no longer read);
-        // past the list a slot reads as stopped (stop 0)
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 1.f, 0.f);
-        if (pn >= 0) {
-          const float4 g = s_g[pn];
-          A = make_float4(g.x, g.y, g.z, __uint_as_float(s_stop[pn]));
-          B = make_float4((float)(tc.tx * TW + pn % TW) + 0.5f, (float)(tc.ty * TH + pn / TW) + 0.5f, kn.x,
-                          g.w - (kn.y * g.x + kn.z * g.y + kn.w * g.z));
-        }
-        ra[(s0 + lane) & (kSplatRing - 1)] = A;
-        rb[(s0 + lane) & (kSplatRing - 1)] = B;
-        fetch(s0 + 32 + lane);
-        __syncwarp();
-      }
-      const int s1 = min(s0 + 32, nl + 31);
-#pragma unroll 2
-      for (int s = s0; s < s1; ++s) {
-        const int ic = (s - lane) & (kSplatRing - 1);
-        const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
-        const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
-        const float4 q = rb[ic];
-        const float4 g = ra[ic];
-        T = lane == 0 ? q.z : Tin;
-        Rr = lane == 0 ? q.w : Rin;
-        // a list position before the pixel's stop (false on stopped slots and for
-        // lanes without an entry, since every stop index is at most the list length)
-        const Falloff f = falloff(xy.x, xy.y, co.x, co.y, co.z, co.w, q.x, q.y);
-        if (jj < __float_as_uint(g.w) && f.alpha >= kAlphaMin) {
-          const float one_m = __fsub_rn(1.f, f.alpha);
-          const float w = f.alpha * T;
-          const float cd = c.x * g.x + c.y * g.y + c.z * g.z;
-          Rr = fmaf(-cd, w, Rr);
-          const float dLda = T * cd - __fdividef(Rr, one_m);
-          T = __fmul_rn(T, one_m);
-          v[6] = fmaf(g.x, w, v[6]);
-          v[7] = fmaf(g.y, w, v[7]);
-          v[8] = fmaf(g.z, w, v[8]);
-          const float m = f.raw <= kAlphaMax ? dLda * f.G : 0.f;
-          const float mt = m * f.t, mdy = m * f.dy;
-          v[0] += mt;
-          v[1] += mdy;
-          v[2] = fmaf(mt, f.t, v[2]);
-          v[3] = fmaf(mt, f.dy, v[3]);
-          v[4] = fmaf(mdy, f.dy, v[4]);
-          v[5] += m;
-        }
-      }
-      __syncwarp();   // this chunk's reads before the next chunk's ring writes
-    }
-    if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
-                v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
-      const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
-      red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
-      red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
-      red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
-    }
-    __syncwarp();   // the next bucket rewrites this warp's live list
-    uint32_t nxt = 0;
-    if (lane == 0) nxt = atomicAdd(&s_next, 1u);
-    b = part + kSplatSplit * (int)__shfl_sync(0xffffffffu, nxt, 0);
-  }
-}
-
-#ifndef GS_SPLAT2_BLOCKS
-#define GS_SPLAT2_BLOCKS 7
-#endif
-constexpr int kSplat2Blocks = GS_SPLAT2_BLOCKS;   // resident CTAs per SM the register budget allows
+constexpr int kSplatBlocks = 6;    // resident CTAs per SM the register budget targets (80 registers)
 
 // rcp.approx.ftz.f32: the reciprocal __fdividef uses.
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -798,18 +639,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// The per-splat backward with two live pixels per lane and step: the bucket's live
-// pixels are taken in pairs (2 i, 2 i + 1) and the pairs flow through the warp
-// diagonally as single pixels do in raster_bwd_splat_kernel (at step s lane l works on
-// pair s - l, with both pixels' (T, R) from lane l - 1). The two pixels are
-// independent, so every FP32 operation of a step is a packed pair (fma/mul/add/sub
-// .rn.f32x2), which halves the step's issue slots where the per-pixel work was one
-// scalar chain. The ring holds pairs interleaved, (a, b) in adjacent lanes of each
-// float4, so the shared-memory loads deliver packed operands directly. A pixel's
-// falloff, floor and stop decisions are the forward's own (same operations, same
-// roundings); accumulations differ from the one-pixel kernel only in summation order.
 template <int TW, int TH>
-__global__ void __launch_bounds__(kSplatThreads, kSplat2Blocks) raster_bwd_splat2_kernel(
+__global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
@@ -823,7 +654,7 @@ __global__ void __launch_bounds__(kSplatThreads, kSplat2Blocks) raster_bwd_splat
   // ring of pixel pairs (a, b) at pair index i % 64:
   //   r0 = (gx_a, gx_b, gy_a, gy_b)   r1 = (gz_a, gz_b, stop_a, stop_b)
   //   r2 = (x_a, x_b, y_a, y_b)       r3 = (T_a, T_b, R_a, R_b) at the bucket start
-  __shared__ float4 s_r0[NW][kSplatRing], s_r1[NW][kSplatRing], s_r2[NW][kSplatRing], s_r3[NW][kSplatRing];
+  __shared__ float4 s_ring[NW][4][kSplatRing];     // r0..r3: one base, immediate offsets
   __shared__ uint32_t s_max, s_next;
   const int tile = blockIdx.x / kSplatSplit, part = blockIdx.x % kSplatSplit;
   const TileCoord tc = tile_coord(cams, n_views, tile);
@@ -862,7 +693,7 @@ __global__ void __launch_bounds__(kSplatThreads, kSplat2Blocks) raster_bwd_splat
   const int nb = (n + 31) >> 5;
   const uint64_t bk0 = ckpt_bucket(rg.x, tile);
   uint16_t *live = s_live[warp];
-  float4 *r0 = s_r0[warp], *r1 = s_r1[warp], *r2 = s_r2[warp], *r3 = s_r3[warp];
+  float4 *r0 = s_ring[warp][0], *r1 = s_ring[warp][1], *r2 = s_ring[warp][2], *r3 = s_ring[warp][3];
   for (int b = part + kSplatSplit * warp; b < nb;) {
     const int j = 32 * b + lane;   // this lane's list position
     const bool has = j < n;
@@ -949,12 +780,13 @@ __global__ void __launch_bounds__(kSplatThreads, kSplat2Blocks) raster_bwd_splat
         __syncwarp();
       }
       const int s1 = min(s0 + 32, npair + 31);
-#pragma unroll 2
+      const float4 *rw = s_ring[warp][0];
+#pragma unroll 4
       for (int s = s0; s < s1; ++s) {
-        const int ic = (s - lane) & (kSplatRing - 1);
+        const float4 *q = rw + ((s - lane) & (kSplatRing - 1));
         const float Ta = __shfl_up_sync(0xffffffffu, T.x, 1), Tb = __shfl_up_sync(0xffffffffu, T.y, 1);
         const float Ra = __shfl_up_sync(0xffffffffu, Rr.x, 1), Rb = __shfl_up_sync(0xffffffffu, Rr.y, 1);
-        const float4 q0 = r0[ic], q1 = r1[ic], q2 = r2[ic], q3 = r3[ic];
+        const float4 q0 = q[0], q1 = q[kSplatRing], q2 = q[2 * kSplatRing], q3 = q[3 * kSplatRing];
         T = lane == 0 ? f2(q3.x, q3.y) : f2(Ta, Tb);
         Rr = lane == 0 ? f2(q3.z, q3.w) : f2(Ra, Rb);
         // falloff at both pixels: the forward's operations and roundings
@@ -1096,11 +928,7 @@ static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins
   GS_CUDA_TRY(cudaMemsetAsync(g->d_mean2d, 0, R * 2 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_conic_opacity, 0, R * 4 * sizeof(float), s));
   GS_CUDA_TRY(cudaMemsetAsync(g->d_rgb, 0, R * 4 * sizeof(float), s));
-#ifdef GS_SPLAT_ONE_PIXEL
   raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
-#else
-  raster_bwd_splat2_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
-#endif
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
