@@ -271,6 +271,7 @@ __device__ __forceinline__ uint32_t band_columns(float xl, float xr, int x0, int
 // digit's entries stay in depth order.
 constexpr int kMaxFusedBits = 8;
 constexpr int kUnits = 64;
+constexpr int kWinCap = 256;   // 32-hit windows per round located by bit masks (else a binary search)
 
 template <bool EMIT>
 __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32_t *__restrict__ order,
@@ -283,6 +284,8 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
   __shared__ BinRec s_rec[8][32];
   __shared__ uint2 s_unit[8][kUnits];            // (record slot << 24 | run length, tile id of the run's first column)
   __shared__ uint32_t s_hpre[8][kUnits + 1];     // exclusive scan of the run lengths
+  __shared__ uint32_t s_mask[8][kWinCap];        // per 32-hit window: bits at the hits that start a unit
+  __shared__ uint8_t s_uid[8][kUnits];           // k-th non-empty unit of the round
   __shared__ uint32_t s_cur[8][1 << kMaxFusedBits];
   if (EMIT && *overflow) return;
   const uint32_t nv = *n_vis;
@@ -389,19 +392,49 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
         if (lane == 0) s_hpre[wib][kUnits] = total;
         __syncwarp();
         const uint32_t nu = min((uint32_t)kUnits, n_units - u0);
+        // the unit of hit h is the last non-empty one starting at or before h: mark the
+        // starts in per-window bit masks and number the non-empty units, so that a lane
+        // finds its unit by a popcount instead of a binary search over s_hpre
+        const uint32_t nwin = (total + 31) >> 5;
+        const bool masks = nwin <= (uint32_t)kWinCap;
+        if (masks) {
+          for (uint32_t w = lane; w < nwin; w += 32) s_mask[wib][w] = 0u;
+          __syncwarp();
+          uint32_t kbase = 0;
+#pragma unroll
+          for (int i = 0; i < kUnits / 32; ++i) {
+            const bool ne = run[i] > 0;
+            const uint32_t bal = __ballot_sync(0xffffffffu, ne);
+            if (ne) {
+              const uint32_t pos = s_hpre[wib][32 * i + lane];
+              atomicOr(&s_mask[wib][pos >> 5], 1u << (pos & 31));
+              s_uid[wib][kbase + __popc(bal & lt)] = (uint8_t)(32 * i + lane);
+            }
+            kbase += __popc(bal);
+          }
+          __syncwarp();
+        }
+        const uint32_t le = lt | (1u << lane);
+        uint32_t starts = 0;   // non-empty units starting before the window
         for (uint32_t h0 = 0; h0 < total; h0 += 32) {
           const uint32_t h = h0 + lane;
           const bool hit = h < total;
-          uint32_t tile = 0, r = 0;
-          if (hit) {
-            // unit: the last one whose hits start at or before h
+          uint32_t tile = 0, r = 0, u = 0;
+          if (masks) {
+            const uint32_t m = s_mask[wib][h0 >> 5];
+            u = s_uid[wib][starts + __popc(m & le) - 1u];
+            starts += __popc(m);
+          } else if (hit) {
             uint32_t lo = 0, hi = nu;   // invariant: s_hpre[lo] <= h < s_hpre[hi]
             while (hi - lo > 1) {
               const uint32_t mid = (lo + hi) >> 1;
               if (s_hpre[wib][mid] <= h) lo = mid; else hi = mid;
             }
-            const uint2 un = s_unit[wib][lo];
-            tile = un.y + (h - s_hpre[wib][lo]);
+            u = lo;
+          }
+          if (hit) {
+            const uint2 un = s_unit[wib][u];
+            tile = un.y + (h - s_hpre[wib][u]);
             r = s_rec[wib][un.x >> 24].rec;
           }
           const uint32_t dig = tile & dmask;

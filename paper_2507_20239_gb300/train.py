@@ -20,6 +20,7 @@ use rises by one every `sh_every` steps up to the coefficients stored.
 """
 from __future__ import annotations
 
+import json
 import math
 from dataclasses import dataclass, field
 from typing import Callable, Optional
@@ -186,8 +187,50 @@ class Trainer:
                 "max_clones": int(c.max().item()) if self.n else 0,
                 "origins_alive": int(torch.unique(self.prov["origin"]).numel())}
 
-    def run(self, log_every: int = 100):
-        for it in range(1, self.sched.total + 1):
+    # ---------------------------------------------------------------- checkpoint / resume
+    def state_dict(self, next_it: int) -> dict:
+        """Everything training needs to continue at iteration next_it, on the host:
+        parameters, Adam moments and step count, densification statistics,
+        provenance, the densification event counter and the history so far."""
+        host = lambda t: t.detach().cpu().numpy()
+        st = {f"param.{k}": host(self.P[k]) for k in PARAM_KEYS}
+        st.update({f"moment.{k}": host(v) for k, v in self.opt.moments().items()})
+        st.update({"stats.accum": host(self.stats.accum), "stats.count": host(self.stats.count)})
+        st.update({f"prov.{k}": host(v) for k, v in self.prov.items()})
+        st["meta"] = np.array(json.dumps({"next_it": int(next_it), "adam_t": int(self.opt.t), "event": int(self.event),
+                                          "history": self.history, "events": self.events,
+                                          "lrs": self.lrs}))
+        return st
+
+    def save(self, path: str, next_it: int):
+        """Write state_dict(next_it) to path (numpy .npz, uncompressed)."""
+        np.savez(path, **self.state_dict(next_it))
+
+    def load(self, path: str) -> int:
+        """Restore a state written by save(); returns the iteration to continue at."""
+        z = np.load(path, allow_pickle=False)
+        meta = json.loads(str(z["meta"]))
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(self.device)
+        params = {k: dev(z[f"param.{k}"]) for k in PARAM_KEYS}
+        moments = {k[len("moment."):]: dev(z[k]) for k in z.files if k.startswith("moment.")}
+        self._set_params(params, moments, meta["adam_t"])
+        self.stats.accum.copy_(dev(z["stats.accum"]))
+        self.stats.count.copy_(dev(z["stats.count"]))
+        self.prov = {k: dev(z[f"prov.{k}"]) for k in R.PROV_KEYS}
+        self.event = int(meta["event"])
+        self.history = [tuple(h) for h in meta["history"]]
+        self.events = [tuple(e) for e in meta["events"]]
+        self.lrs = dict(meta["lrs"])
+        self.opt.lrs = dict(self.lrs)
+        return int(meta["next_it"])
+
+    def run(self, log_every: int = 100, start: int = 1, stop: Optional[int] = None,
+            checkpoint: Optional[str] = None, checkpoint_every: int = 0):
+        """Iterations start..stop (1-based, default to the schedule's end); with
+        checkpoint and checkpoint_every, the state is saved every checkpoint_every
+        iterations (after that iteration's densification and reset)."""
+        stop = self.sched.total if stop is None else stop
+        for it in range(start, stop + 1):
             loss = self.step(it - 1)
             if self.sched.densify_at(it):
                 self.densify(it)
@@ -196,6 +239,8 @@ class Trainer:
                 O.opacity_reset({k: self.P[k].detach() for k in PARAM_KEYS}, self.opt)
             if it % log_every == 0 or it == self.sched.total:
                 self.history.append((it, self.n, float(loss[0].item())))
+            if checkpoint and checkpoint_every and it % checkpoint_every == 0:
+                self.save(checkpoint, it + 1)
         return self.history
 
 
@@ -280,6 +325,10 @@ def main(argv=None):
                     help="adaptive opacity pruning with ratio P (default: fixed tau 0.005)")
     ap.add_argument("--prune-upper", type=float, default=0.05, metavar="TAU_U",
                     help="adaptive pruning's upper bound on tau")
+    ap.add_argument("--checkpoint", default=None, metavar="PATH",
+                    help="save the training state here every --checkpoint-every iterations")
+    ap.add_argument("--checkpoint-every", type=int, default=500)
+    ap.add_argument("--resume", default=None, metavar="PATH", help="continue from a saved training state")
     args = ap.parse_args(argv)
     s = args.steps / 3000.0
     sched = Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (int(1000 * s), 2, R.DENSIFY_SPLIT_ONLY),
@@ -303,7 +352,8 @@ def main(argv=None):
     else:
         init = synth.surface_scene(3, args.init, 3, log_scale_mean=args.init_log_scale).params()
     tr = Trainer(init, views, sched, extent=1.1 * 4.0)
-    hist = tr.run()
+    start = tr.load(args.resume) if args.resume else 1
+    hist = tr.run(start=start, checkpoint=args.checkpoint, checkpoint_every=args.checkpoint_every)
     n_split = sum(e[2] for e in tr.events)
     n_clone = sum(e[3] for e in tr.events)
     print(json.dumps({"history": hist, "final_n": tr.n, "events": tr.events,

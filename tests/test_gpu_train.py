@@ -95,3 +95,36 @@ def test_adaptive_opacity_pruning_in_training():
     assert sum(e[5] for e in events) > 0
     assert all(e[5] <= math.floor(0.03 * (e[4] + e[5])) for e in events)
     assert hist[-1][2] < hist[0][2]
+
+
+def test_checkpoint_resume_continues_training(tmp_path):
+    """Training saved at iteration 150 and resumed in a fresh trainer: the restored
+    state (parameters, Adam moments and step count, densification statistics,
+    provenance, event counter, history) equals the saved one bit for bit, and the
+    resumed run densifies at the same iterations as the uninterrupted one, to the
+    same size up to the run-to-run spread of the atomically summed gradients."""
+    from paper_2507_20239_gb300 import train as T
+    gt = synth.surface_scene(13, 60_000, 3)
+    cams = T.orbit_views(4, 320, 212, 320.0)
+    views = {r: (c, T.render_targets(gt.params(), 3, c)) for r, c in cams.items()}
+    init = synth.sfm_like_init(gt, 8_000, seed=3).params()
+    sched = T.Schedule(stages=[(0, 4, R.DENSIFY_SPLIT_ONLY), (100, 2, R.DENSIFY_SPLIT_ONLY),
+                               (200, 1, R.DENSIFY_ADAPTIVE)], total=300, densify_from=50,
+                       densify_until=250, densify_every=50, sh_every=75)
+    path = str(tmp_path / "state.npz")
+    a = T.Trainer(init, views, sched, extent=1.1 * 4.0)
+    a.run(log_every=50, stop=150, checkpoint=path, checkpoint_every=150)
+    saved = a.state_dict(151)
+    b = T.Trainer(init, views, sched, extent=1.1 * 4.0)
+    start = b.load(path)
+    assert start == 151
+    restored = b.state_dict(151)
+    assert set(saved) == set(restored)
+    for k in saved:
+        assert np.array_equal(saved[k], restored[k]), k
+    a.run(log_every=50, start=151)
+    b.run(log_every=50, start=151)
+    assert [e[0] for e in a.events] == [e[0] for e in b.events] == [50, 100, 150, 200, 250]
+    assert abs(a.n - b.n) <= 0.02 * a.n, (a.n, b.n)
+    assert b.history[-1][0] == 300 and b.history[-1][2] < b.history[0][2]
+    assert int(b.prov["origin"].max()) < 8_000 and int(b.prov["origin"].min()) >= 0
