@@ -129,6 +129,10 @@ typedef struct {
   int32_t stage_depth;     /* gs_raster_bwd: list entries staged per CTA step,
                             * 0 = one per thread, 1 = half as many. A tuning
                             * knob: gradients agree up to summation order. */
+  uint32_t *d_queue;       /* gs_raster_fwd / gs_raster_fwd_ckpt: NULL = one CTA
+                            * per tile; else a device word (overwritten) that a
+                            * persistent grid's warps claim (tile, 8x8 block)
+                            * units from. A tuning knob: images are identical. */
 } gs_raster_cfg_t;
 
 /* Gradients of the loss w.r.t. the projected records (device, [R] rows, same row

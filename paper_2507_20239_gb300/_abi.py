@@ -38,7 +38,8 @@ class GsBins(C.Structure):
 
 
 class GsRasterCfg(C.Structure):
-    _fields_ = [("bg", C.c_float * 3), ("store_stop", C.c_int32), ("stage_depth", C.c_int32)]
+    _fields_ = [("bg", C.c_float * 3), ("store_stop", C.c_int32), ("stage_depth", C.c_int32),
+                ("d_queue", vp)]
 
 
 class GsRecGrads(C.Structure):

@@ -3,7 +3,8 @@
 For a given scene size and set of view resolutions it times the whole step
 (TrainStep, graph-replayed) for every candidate StepConfig -- tile shape, the
 low tile-id bits the binning sorts while emitting, the backward's staging
-depth, and the per-pixel or per-splat backward -- and keeps the fastest. None of the knobs changes the rendered images
+depth, the per-pixel or per-splat backward, and the forward as one CTA per tile or
+as a persistent grid claiming (tile, block) units -- and keeps the fastest. None of the knobs changes the rendered images
 (every candidate's images are compared with the first one's); the gradients agree
 up to summation order. Results are cached per (device, Gaussians, SH degree, view
 sizes, candidates) for the life of the process.
@@ -23,9 +24,10 @@ TILES = ((16, 16), (8, 8), (16, 32))
 
 
 def default_candidates(tiles: Sequence = TILES, fused_bits: Sequence = (0, 8),
-                       stage_depths: Sequence = (0, 1), splat: bool = True) -> list:
+                       stage_depths: Sequence = (0, 1), splat: bool = True, queue: bool = True) -> list:
     """Every (tile, fused bits) pair with each staging depth of the per-pixel
-    backward and, if splat, once with the per-splat backward."""
+    backward and, if splat, once with the per-splat backward; with queue, the
+    per-splat candidates also with the forward as a persistent (tile, block) queue."""
     out = []
     for t, f in itertools.product(tiles, fused_bits):
         if not lib().gs_tile_supported(int(t[0]), int(t[1])):
@@ -35,6 +37,8 @@ def default_candidates(tiles: Sequence = TILES, fused_bits: Sequence = (0, 8),
             out.append(StepConfig(tile=tile, sort_fused_bits=int(f), stage_depth=int(s)))
         if splat:
             out.append(StepConfig(tile=tile, sort_fused_bits=int(f), backward="splat"))
+            if queue:
+                out.append(StepConfig(tile=tile, sort_fused_bits=int(f), backward="splat", queue=True))
     return out
 
 

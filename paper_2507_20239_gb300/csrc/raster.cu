@@ -168,21 +168,34 @@ __device__ __forceinline__ int warp_select(const float4 *s_rgb, int cnt, int war
 // passing entries in list order. A warp leaves as soon as its 64 pixels have
 // stopped, so neither barriers nor finished neighbours hold it (one-warp CTAs,
 // which also free a finished warp's slot, measured no faster).
+struct FwdArgs {
+  const float2 *__restrict__ mean2d;
+  const float4 *__restrict__ conic_o;
+  const float4 *__restrict__ rgb;
+  const uint32_t *__restrict__ vals;
+  const uint2 *__restrict__ ranges;
+  const gs_camera_t *__restrict__ cams;
+  int n_views;
+  float bg0, bg1, bg2;
+  float *__restrict__ image;
+  float *__restrict__ T_final;
+  uint32_t *__restrict__ stop_out;
+  CkptLayout ckpt;
+};
+
+// One warp's 8 x 8 block `warp` of `tile`, with the warp's staging slots.
 template <int TW, int TH, bool CKPT>
-__global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
-    const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
-    const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
-    int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
-    uint32_t *__restrict__ stop_out, CkptLayout ckpt) {
+__device__ __forceinline__ void fwd_warp_block(const FwdArgs &a, int tile, int warp, int lane, float2 *sxy,
+                                               float4 *sco, float4 *srgb) {
   constexpr int NW = TW * TH / 64;
-  __shared__ float2 s_xy[NW][32];
-  __shared__ float4 s_co[NW][32];
-  __shared__ float4 s_rgb[NW][32];
-  const int tile = blockIdx.x;
-  const TileCoord tc = tile_coord(cams, n_views, tile);
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const float2 *__restrict__ mean2d = a.mean2d;
+  const float4 *__restrict__ conic_o = a.conic_o;
+  const float4 *__restrict__ rgb = a.rgb;
+  const uint32_t *__restrict__ vals = a.vals;
+  const CkptLayout &ckpt = a.ckpt;
+  const TileCoord tc = tile_coord(a.cams, a.n_views, tile);
   int lx, ly;
-  pixel_of<TW>(t, lx, ly);
+  pixel_of<TW>(warp * 32 + lane, lx, ly);
   const int py = tc.ty * TH + ly;
   const int px = tc.tx * TW + lx;
   const bool in0 = py < tc.H && px < tc.W, in1 = py < tc.H && px + 1 < tc.W;
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   float2 T = f2(1.f), cr = f2(0.f), cg = f2(0.f), cb = f2(0.f);   // (pixel 0, pixel 1)
   uint32_t st0 = 0, st1 = 0;
   bool done0 = !in0, done1 = !in1;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = a.ranges[tile];
   const int n = (int)(rg.y - rg.x);
   // software pipeline: the record id two steps ahead, the record one step ahead
   uint32_t r_next = lane < n ? vals[rg.x + lane] : 0u;
@@ -251,9 +264,9 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
       float xl, xr;
       sel = row_span(e, Y0, Y1, xl, xr) && X1 >= xl && X0 <= xr;
       if (sel) {
-        s_xy[warp][lane] = xy;
-        s_co[warp][lane] = make_float4(__fmul_rn(co.x, kNegHalfLog2e), co.y, __fmul_rn(co.z, kNegHalfLog2e), co.w);
-        s_rgb[warp][lane] = c;
+        sxy[lane] = xy;
+        sco[lane] = make_float4(__fmul_rn(co.x, kNegHalfLog2e), co.y, __fmul_rn(co.z, kNegHalfLog2e), co.w);
+        srgb[lane] = c;
       }
     }
     uint32_t b = __ballot_sync(0xffffffffu, sel);
@@ -264,8 +277,8 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
     while (b) {
       const int i = __ffs(b) - 1;
       b &= b - 1u;
-      const float2 xy = s_xy[warp][i];
-      const float4 co = s_co[warp][i];
+      const float2 xy = sxy[i];
+      const float4 co = sco[i];
       const Falloff2 f = falloff2(xy.x, xy.y, co.x, co.y, co.z, co.w, fx, fy);
       const bool a0 = !done0 && f.alpha.x >= kAlphaMin, a1 = !done1 && f.alpha.y >= kAlphaMin;
       const float2 Tn = f2_mul(T, f2_sub(f2(1.f), f.alpha));
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
       done0 = done0 || (a0 && !c0);
       done1 = done1 || (a1 && !c1);
       const float2 w = f2_mul(f2(c0 ? f.alpha.x : 0.f, c1 ? f.alpha.y : 0.f), T);
-      const float4 c = s_rgb[warp][i];
+      const float4 c = srgb[i];
       cr = f2_fma(f2(c.x), w, cr);
       cg = f2_fma(f2(c.y), w, cg);
       cb = f2_fma(f2(c.z), w, cb);
@@ -287,20 +300,56 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(
   const float r0 = cr.x, g0 = cg.x, b0 = cb.x, r1 = cr.y, g1 = cg.y, b1 = cb.y;
   const int64_t p0 = (int64_t)py * tc.W + px;
   const int64_t plane = (int64_t)tc.W * tc.H;
-  float *img = image + 3 * tc.pix_off;
+  float *img = a.image + 3 * tc.pix_off;
   if (in0) {
-    img[p0] = fmaf(T0, bg0, r0);
-    img[plane + p0] = fmaf(T0, bg1, g0);
-    img[2 * plane + p0] = fmaf(T0, bg2, b0);
-    T_final[tc.pix_off + p0] = T0;
-    if (stop_out) stop_out[tc.pix_off + p0] = st0;
+    img[p0] = fmaf(T0, a.bg0, r0);
+    img[plane + p0] = fmaf(T0, a.bg1, g0);
+    img[2 * plane + p0] = fmaf(T0, a.bg2, b0);
+    a.T_final[tc.pix_off + p0] = T0;
+    if (a.stop_out) a.stop_out[tc.pix_off + p0] = st0;
   }
   if (in1) {
-    img[p0 + 1] = fmaf(T1, bg0, r1);
-    img[plane + p0 + 1] = fmaf(T1, bg1, g1);
-    img[2 * plane + p0 + 1] = fmaf(T1, bg2, b1);
-    T_final[tc.pix_off + p0 + 1] = T1;
-    if (stop_out) stop_out[tc.pix_off + p0 + 1] = st1;
+    img[p0 + 1] = fmaf(T1, a.bg0, r1);
+    img[plane + p0 + 1] = fmaf(T1, a.bg1, g1);
+    img[2 * plane + p0 + 1] = fmaf(T1, a.bg2, b1);
+    a.T_final[tc.pix_off + p0 + 1] = T1;
+    if (a.stop_out) a.stop_out[tc.pix_off + p0 + 1] = st1;
+  }
+}
+
+// One CTA per tile, warp w on the tile's block w.
+template <int TW, int TH, bool CKPT>
+__global__ void __launch_bounds__(TW *TH / 2) raster_fwd_warp_kernel(const FwdArgs a) {
+  constexpr int NW = TW * TH / 64;
+  __shared__ float2 s_xy[NW][32];
+  __shared__ float4 s_co[NW][32];
+  __shared__ float4 s_rgb[NW][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  fwd_warp_block<TW, TH, CKPT>(a, blockIdx.x, warp, lane, s_xy[warp], s_co[warp], s_rgb[warp]);
+}
+
+// Persistent form: a resident grid whose warps claim (tile, block) units from a
+// counter (zeroed before the launch) in tile order, so that a warp whose block
+// stopped early takes the next unit instead of idling until its CTA's slowest warp
+// is done. Units are independent; no warp ever waits on another.
+constexpr int kQueueWarps = 4;
+
+template <int TW, int TH, bool CKPT>
+__global__ void __launch_bounds__(32 * kQueueWarps) raster_fwd_queue_kernel(const FwdArgs a, int n_tiles,
+                                                                           uint32_t *queue) {
+  constexpr int NW = TW * TH / 64;
+  __shared__ float2 s_xy[kQueueWarps][32];
+  __shared__ float4 s_co[kQueueWarps][32];
+  __shared__ float4 s_rgb[kQueueWarps][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t units = (uint32_t)n_tiles * NW;
+  for (;;) {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(queue, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;
+    fwd_warp_block<TW, TH, CKPT>(a, (int)(u / NW), (int)(u % NW), lane, s_xy[w], s_co[w], s_rgb[w]);
+    __syncwarp();
   }
 }
 
@@ -871,15 +920,33 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
                               const gs_raster_cfg_t *cfg, float *image, float *T_final, uint32_t *stop,
                               cudaStream_t s, uint32_t *counts = nullptr, const CkptLayout *ckpt = nullptr) {
   if (!COUNT) {
-    const CkptLayout ck = ckpt ? *ckpt : CkptLayout{};
-#define GS_FWD(CK)                                                                                           \
-  raster_fwd_warp_kernel<TW, TH, CK><<<frame->n_tiles, TW * TH / 2, 0, s>>>(                                  \
-      reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),   \
-      reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),  \
-      frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,                    \
-      cfg->store_stop ? stop : nullptr, ck)
-    ckpt ? GS_FWD(true) : GS_FWD(false);
-#undef GS_FWD
+    FwdArgs a;
+    a.mean2d = reinterpret_cast<const float2 *>(proj->mean2d);
+    a.conic_o = reinterpret_cast<const float4 *>(proj->conic_opacity);
+    a.rgb = reinterpret_cast<const float4 *>(proj->rgb);
+    a.vals = bins->vals;
+    a.ranges = reinterpret_cast<const uint2 *>(bins->ranges);
+    a.cams = frame->cams_dev;
+    a.n_views = frame->n_views;
+    a.bg0 = cfg->bg[0];
+    a.bg1 = cfg->bg[1];
+    a.bg2 = cfg->bg[2];
+    a.image = image;
+    a.T_final = T_final;
+    a.stop_out = cfg->store_stop ? stop : nullptr;
+    a.ckpt = ckpt ? *ckpt : CkptLayout{};
+    if (cfg->d_queue) {
+      // persistent grid: every CTA the SMs hold at once
+      GS_CUDA_TRY(cudaMemsetAsync(cfg->d_queue, 0, sizeof(uint32_t), s));
+      auto kern = ckpt ? raster_fwd_queue_kernel<TW, TH, true> : raster_fwd_queue_kernel<TW, TH, false>;
+      int per_sm = 0;
+      GS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kQueueWarps, 0));
+      if (per_sm < 1) per_sm = 1;
+      kern<<<num_sms() * per_sm, 32 * kQueueWarps, 0, s>>>(a, frame->n_tiles, cfg->d_queue);
+    } else {
+      auto kern = ckpt ? raster_fwd_warp_kernel<TW, TH, true> : raster_fwd_warp_kernel<TW, TH, false>;
+      kern<<<frame->n_tiles, TW * TH / 2, 0, s>>>(a);
+    }
     GS_LAUNCH_CHECK();
     return GS_OK;
   }

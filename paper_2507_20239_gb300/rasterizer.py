@@ -224,23 +224,26 @@ def bin_sort(proj: Projected, frame: Frame, capacity: Optional[int] = None, want
 
 
 # ----------------------------------------------------------------------------------------
-def raster_cfg(bg=(0.0, 0.0, 0.0), store_stop=False, stage_depth=0) -> _abi.GsRasterCfg:
+def raster_cfg(bg=(0.0, 0.0, 0.0), store_stop=False, stage_depth=0, queue=None) -> _abi.GsRasterCfg:
+    """queue: None (one CTA per tile) or a device int32 [1] tensor for the forward's
+    persistent grid to claim its (tile, block) units from."""
     c = _abi.GsRasterCfg()
     for k in range(3):
         c.bg[k] = float(bg[k])
     c.store_stop = 1 if store_stop else 0
     c.stage_depth = int(stage_depth)
+    c.d_queue = None if queue is None else _need(queue, torch.int32, "queue").data_ptr()
     return c
 
 
 def raster_fwd(proj: Projected, bins: Bins, frame: Frame, bg=(0.0, 0.0, 0.0), store_stop=False,
-               image=None, T_final=None, stop=None, stream=None):
+               image=None, T_final=None, stop=None, stream=None, queue=None):
     dev = frame.device
     image = torch.empty(3 * frame.n_pixels, dtype=torch.float32, device=dev) if image is None else image
     T_final = torch.empty(frame.n_pixels, dtype=torch.float32, device=dev) if T_final is None else T_final
     if store_stop and stop is None:
         stop = torch.empty(frame.n_pixels, dtype=torch.int32, device=dev)
-    cfg = raster_cfg(bg, store_stop)
+    cfg = raster_cfg(bg, store_stop, queue=queue)
     check(lib().gs_raster_fwd(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame),
                               C.byref(cfg), _p(image), _p(T_final), _p(stop) if store_stop else None,
                               _stream(stream)), "gs_raster_fwd")
@@ -272,13 +275,13 @@ def ckpt_usage(frame: Frame, bins: "Bins", ckpt: torch.Tensor, out=None, stream=
 
 
 def raster_fwd_ckpt(proj: Projected, bins: Bins, frame: Frame, ckpt: torch.Tensor, bg=(0.0, 0.0, 0.0),
-                    image=None, T_final=None, stop=None, stream=None):
+                    image=None, T_final=None, stop=None, stream=None, queue=None):
     """raster_fwd with stop indices and the per-splat backward's checkpoints."""
     dev = frame.device
     image = torch.empty(3 * frame.n_pixels, dtype=torch.float32, device=dev) if image is None else image
     T_final = torch.empty(frame.n_pixels, dtype=torch.float32, device=dev) if T_final is None else T_final
     stop = torch.empty(frame.n_pixels, dtype=torch.int32, device=dev) if stop is None else stop
-    cfg = raster_cfg(bg, True)
+    cfg = raster_cfg(bg, True, queue=queue)
     check(lib().gs_raster_fwd_ckpt(C.byref(proj.struct()), C.byref(bins.struct()), C.byref(frame.frame),
                                    C.byref(cfg), _p(image), _p(T_final), _p(stop), _p(ckpt),
                                    ckpt.numel() * ckpt.element_size(), _stream(stream)), "gs_raster_fwd_ckpt")

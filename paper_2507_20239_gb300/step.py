@@ -41,15 +41,17 @@ class StepConfig:
     sort_fused_bits: int = 0
     stage_depth: int = 0
     backward: str = "pixel"
+    queue: bool = False      # the forward as a persistent grid claiming (tile, block) units
 
     def __post_init__(self):
         if self.backward not in BACKWARDS:
             raise ValueError(f"backward must be one of {BACKWARDS}, not {self.backward!r}")
 
     def label(self) -> str:
+        q = "/queue" if self.queue else ""
         if self.backward == "splat":
-            return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/splat"
-        return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/s{self.stage_depth}"
+            return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/splat{q}"
+        return f"{self.tile[0]}x{self.tile[1]}/f{self.sort_fused_bits}/s{self.stage_depth}{q}"
 
 
 def duplicates(params: dict, sh_degree: int, frame: R.Frame) -> int:
@@ -95,6 +97,7 @@ class TrainStep:
                 slots = int(ckpt_slots(params, sh_degree, f, capacity) * headroom) + 4 * 256
             self.ckpt = R.alloc_ckpt(f, self.bins, slots)
             self.ckpt_use = torch.zeros(2, dtype=torch.int64, device=f.device)
+        self.queue = torch.zeros(1, dtype=torch.int32, device=f.device) if config.queue else None
         self.d_image = torch.empty_like(self.image)
         self.loss = torch.empty(f.n_views, device=f.device)
         self.target = f.pack_images(target_images).contiguous()
@@ -113,10 +116,11 @@ class TrainStep:
         R.bin_sort_into(self.proj, f, self.bins)
         rec(2)
         if self.splat:
-            R.raster_fwd_ckpt(self.proj, self.bins, f, self.ckpt, image=self.image, T_final=self.T, stop=self.stop)
+            R.raster_fwd_ckpt(self.proj, self.bins, f, self.ckpt, image=self.image, T_final=self.T, stop=self.stop,
+                              queue=self.queue)
         else:
             R.raster_fwd(self.proj, self.bins, f, image=self.image, T_final=self.T, store_stop=self.store_stop,
-                         stop=self.stop)
+                         stop=self.stop, queue=self.queue)
         rec(3)
         R.l1_loss_grad(f, self.image, self.target, d_image=self.d_image, loss=self.loss)
         rec(4)

@@ -46,7 +46,7 @@ STRUCTS = {
     "gs_params_t": (_abi.GsParams, ["means", "sh", "n", "sh_degree", "sh_stride"]),
     "gs_proj_t": (_abi.GsProj, ["mean2d", "clamped", "n_records"]),
     "gs_bins_t": (_abi.GsBins, ["vals", "keys", "ranges", "d_count", "capacity"]),
-    "gs_raster_cfg_t": (_abi.GsRasterCfg, ["bg", "store_stop"]),
+    "gs_raster_cfg_t": (_abi.GsRasterCfg, ["bg", "store_stop", "stage_depth", "d_queue"]),
     "gs_rec_grads_t": (_abi.GsRecGrads, ["d_mean2d", "d_rgb"]),
     "gs_param_grads_t": (_abi.GsParamGrads, ["d_means", "d_sh"]),
     "gs_densify_cfg_t": (_abi.GsDensifyCfg, ["mode", "prune_upper_logit", "prune_ratio", "seed", "event"]),

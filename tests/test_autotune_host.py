@@ -44,15 +44,19 @@ def test_default_candidates_cover_the_tile_shapes():
     c = at.default_candidates()
     assert {x.tile for x in c} == {(16, 16), (8, 8), (16, 32)}
     assert {x.stage_depth for x in c if x.backward == "pixel"} == {0, 1}
-    # per (tile, fused bits): two per-pixel staging depths and the per-splat backward
-    assert sum(x.backward == "splat" for x in c) == 6
-    assert len(set(c)) == len(c) == 18
-    assert len({x.label() for x in c}) == 18
+    # per (tile, fused bits): two per-pixel staging depths and the per-splat backward,
+    # the latter with the per-tile and with the queued forward
+    assert sum(x.backward == "splat" for x in c) == 12
+    assert sum(x.queue for x in c) == 6 and all(x.backward == "splat" for x in c if x.queue)
+    assert len(set(c)) == len(c) == 24
+    assert len({x.label() for x in c}) == 24
     assert len(at.default_candidates(splat=False)) == 12
+    assert len(at.default_candidates(queue=False)) == 18
 
 
 def test_step_config_backward_is_validated():
     assert StepConfig((8, 8), 2, 0, "splat").label() == "8x8/f2/splat"
     assert StepConfig((16, 16), 0, 1).label() == "16x16/f0/s1"
+    assert StepConfig((16, 16), 0, 0, "splat", True).label() == "16x16/f0/splat/queue"
     with pytest.raises(ValueError):
         StepConfig(backward="tile")

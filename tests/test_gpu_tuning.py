@@ -27,7 +27,8 @@ def test_knobs_keep_images_and_gradients():
     P = dev_params(sc)
     ref = _run(sc, P, StepConfig())
     cands = default_candidates(tiles=((16, 16), (8, 8), (16, 32)), fused_bits=(0, 2, 8), stage_depths=(0, 1))
-    assert len(cands) == 27          # 9 (tile, bits) pairs x (two staging depths + per-splat)
+    # 9 (tile, bits) pairs x (two staging depths + per-splat, per-tile or queued forward)
+    assert len(cands) == 36
     for cfg in cands + ["recomputed"]:
         st = _run(sc, P, StepConfig(), store_stop=False) if cfg == "recomputed" else _run(sc, P, cfg)
         for v in range(len(sc.cameras)):
@@ -71,3 +72,34 @@ def test_invalid_stage_depth_is_rejected():
     st = _run(sc, P, StepConfig())
     with pytest.raises(RuntimeError):
         R.raster_bwd(st.proj, st.bins, st.frame, st.image, st.d_image, stage_depth=3)
+
+
+@pytest.mark.parametrize("name,tile", [("orbit_small", (16, 16)), ("batched_small", (8, 8)),
+                                       ("batched_small", (16, 32))])
+def test_queued_forward_is_identical(name, tile):
+    """The forward as a persistent grid of warps claiming (tile, 8x8 block) units:
+    the image, transmittance and stop indices of the one-CTA-per-tile forward, bit for
+    bit, with and without checkpoints; the per-splat backward from the queued
+    forward's checkpoints gives the same gradients."""
+    sc = scene(name)
+    frame = R.Frame(sc.cameras, tile=tile)
+    proj = R.project(dev_params(sc), sc.sh_degree, frame)
+    bins = R.bin_sort(proj, frame)
+    q = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a = R.raster_fwd(proj, bins, frame, store_stop=True)
+    b = R.raster_fwd(proj, bins, frame, store_stop=True, queue=q)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert int(q.item()) >= frame.n_tiles * tile[0] * tile[1] // 64      # every unit was claimed
+    ck_a, ck_b = R.alloc_ckpt(frame, bins), R.alloc_ckpt(frame, bins)
+    fa = R.raster_fwd_ckpt(proj, bins, frame, ck_a)
+    fb = R.raster_fwd_ckpt(proj, bins, frame, ck_b, queue=q)
+    for x, y in zip(fa, fb):
+        assert torch.equal(x, y)
+    dg = torch.as_tensor(np.random.default_rng(4).normal(0, 1, fa[0].numel()).astype(np.float32)).cuda()
+    ga = R.raster_bwd_splat(proj, bins, frame, fa[0], dg, fa[2], ck_a)
+    gb = R.raster_bwd_splat(proj, bins, frame, fb[0], dg, fb[2], ck_b)
+    torch.cuda.synchronize()
+    for x, y in ((ga.d_mean2d, gb.d_mean2d), (ga.d_conic_opacity, gb.d_conic_opacity), (ga.d_rgb, gb.d_rgb)):
+        assert rel_l2(x.cpu().numpy(), y.cpu().numpy()) < 1e-6
