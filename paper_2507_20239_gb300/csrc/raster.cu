@@ -6,7 +6,7 @@
 // alpha can reach the 1/255 floor) meets its block. A pixel stops before the entry
 // that would drive its transmittance below 1e-4; a warp leaves once its 64 pixels
 // have stopped. Optionally it stores each pixel's stop index and, for the per-splat
-// backward, a checkpoint (T, composited colour) every 32 list entries.
+// backward, a checkpoint (T, composited colour) every 64 list entries.
 //
 // Both backward kernels re-walk the lists front to back with exactly the forward's
 // FP32 decisions and need, per pixel, only <dL/dout, out>:
@@ -227,18 +227,19 @@ __device__ __forceinline__ void fwd_warp_block(const FwdArgs &a, int tile, int w
   if (CKPT && lane == 0 && n > 0) claim = atomicAdd(ckpt.pools + pool, 1u);
   for (int base = 0; base < n; base += 32) {
     if (__all_sync(0xffffffffu, done0 && done1)) break;
-    if (CKPT) {
+    if (CKPT && (base & 63) == 0) {
       // state before list position base: (T, accumulated colour) for the per-splat
-      // backward, in the slot claimed for (bucket, this warp's 8 x 8 block); the claim
-      // for the next step is issued now and its result used a step later, so the
-      // atomic's round trip overlaps the compositing
+      // backward (whose buckets are 64 entries long), in the slot claimed for (32-entry
+      // step, this warp's 8 x 8 block); the claim for the next checkpoint is issued now
+      // and its result used two steps later, so the atomic's round trip overlaps the
+      // compositing
       uint32_t slot = kCkptNone;
       if (lane == 0) {
         const uint64_t idx = (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * NW + warp;
         if (ckpt.n_slots >= ckpt.table_entries) slot = (uint32_t)idx;      // room for every pair
         else if (claim < ckpt.pool_size) slot = (uint32_t)(pool * ckpt.pool_size + claim);
         ckpt.table[idx] = slot;
-        if (base + 32 < n) claim = atomicAdd(ckpt.pools + pool, 1u);
+        if (base + 64 < n) claim = atomicAdd(ckpt.pools + pool, 1u);
       }
       slot = __shfl_sync(0xffffffffu, slot, 0);
       if (slot != kCkptNone) {
@@ -658,24 +659,22 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
 // Per-splat backward (the per-splat parallel back-propagation of the Taming-3DGS
 // lineage that the paper's base trainer uses): the same gradient as
 // raster_bwd_kernel, parallel over list entries instead of pixels. The warps of a
-// tile's CTAs claim its 32-entry buckets (up to the tile's largest stop index) one
-// at a time, one entry per lane. A bucket's live pixels (stop index beyond its
-// first position) start from the forward's checkpoint (T and the colour composited
-// before the bucket), taken in pairs (2 i, 2 i + 1), and the pairs flow through the
-// warp diagonally: at step s lane l works on pair s - l, taking both pixels' (T, R)
-// from lane l - 1, which handled that pair one step earlier, in list order. The two
-// pixels are independent, so every FP32 operation of a step is a packed pair
-// (add/sub/mul/fma.rn.f32x2), which halves the issue slots of the per-pixel chain.
-// A tile's buckets are shared by kSplatSplit CTAs, so a tile with a long list does
-// not hold the end of the launch. Each lane sums its entry's moments over the tile's
-// pixels in registers and adds them to the record gradients once, with no cross-lane
-// reduction. Since the lanes only ever read 32 consecutive pairs, a warp keeps them
-// in a 64-slot ring refilled every 32 steps (the next 32 pairs' checkpoints are
-// loaded meanwhile); the ring holds each pair interleaved, (a, b) in adjacent lanes of
-// each float4, so the shared-memory loads deliver packed operands directly. A
-// pixel's falloff, floor and stop decisions are the forward's own (same operations,
-// same roundings). Needs the stop indices and the checkpoints written by the forward
-// (gs_raster_fwd_ckpt).
+// tile's CTAs claim its 64-entry buckets (up to the tile's largest stop index) one
+// at a time, two consecutive entries per lane. A bucket's live pixels (stop index
+// beyond its first position) start from the forward's checkpoint (T and the colour
+// composited before the bucket) and flow through the warp diagonally: at step s lane
+// l works on live pixel s - l, taking its (T, R) from lane l - 1, which handled that
+// pixel one step earlier, and passes it through its two entries in list order. The
+// two entries' falloff and their moment sums are independent, so they run as packed
+// FP32 pairs (add/sub/mul/fma.rn.f32x2); only the transmittance chain through the two
+// entries stays scalar. A tile's buckets are shared by kSplatSplit CTAs, so a tile with
+// a long list does not hold the end of the launch. Each lane sums its entries' moments
+// over the tile's pixels in registers and adds them to the record gradients once,
+// with no cross-lane reduction. Since the lanes only ever read 32 consecutive live
+// pixels, a warp keeps them in a 64-slot ring refilled every 32 steps (the next 32
+// pixels' checkpoints are loaded meanwhile). A pixel's falloff, floor and stop
+// decisions are the forward's own (same operations, same roundings). Needs the stop
+// indices and the checkpoints written by the forward (gs_raster_fwd_ckpt).
 constexpr int kSplatThreads = 128;
 constexpr int kSplatSplit = 2;     // CTAs per tile (bucket b goes to CTA b % kSplatSplit)
 constexpr int kSplatRing = 64;
@@ -700,10 +699,9 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
   __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
   __shared__ uint32_t s_stop[NP];
   __shared__ uint16_t s_live[NW][NP];
-  // ring of pixel pairs (a, b) at pair index i % 64:
-  //   r0 = (gx_a, gx_b, gy_a, gy_b)   r1 = (gz_a, gz_b, stop_a, stop_b)
-  //   r2 = (x_a, x_b, y_a, y_b)       r3 = (T_a, T_b, R_a, R_b) at the bucket start
-  __shared__ float4 s_ring[NW][4][kSplatRing];     // r0..r3: one base, immediate offsets
+  // ring of live pixels at index i % 64: ra = (dL/dout, stop bits), rb = (x, y, T, R)
+  // at the bucket start; one base address, immediate offsets
+  __shared__ float4 s_ring[NW][2][kSplatRing];
   __shared__ uint32_t s_max, s_next;
   const int tile = blockIdx.x / kSplatSplit, part = blockIdx.x % kSplatSplit;
   const TileCoord tc = tile_coord(cams, n_views, tile);
@@ -739,130 +737,123 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
   __syncthreads();
   const uint2 rg = ranges[tile];
   const int n = min((int)(rg.y - rg.x), (int)s_max);
-  const int nb = (n + 31) >> 5;
+  const int nb = (n + 63) >> 6;                     // buckets of 64 list entries
   const uint64_t bk0 = ckpt_bucket(rg.x, tile);
   uint16_t *live = s_live[warp];
-  float4 *r0 = s_ring[warp][0], *r1 = s_ring[warp][1], *r2 = s_ring[warp][2], *r3 = s_ring[warp][3];
+  float4 *ra = s_ring[warp][0], *rb = s_ring[warp][1];
+  const float4 *rw = s_ring[warp][0];
   for (int b = part + kSplatSplit * warp; b < nb;) {
-    const int j = 32 * b + lane;   // this lane's list position
-    const bool has = j < n;
-    uint32_t r = 0;
-    float2 xy = make_float2(0.f, 0.f);
-    float4 co = make_float4(0.f, 0.f, 0.f, 0.f), cu = co, c = co;
-    if (has) {
-      r = vals[rg.x + j];
-      xy = mean2d[r];
-      cu = conic_o[r];
-      c = rgb[r];
-      co = make_float4(__fmul_rn(cu.x, kNegHalfLog2e), cu.y, __fmul_rn(cu.z, kNegHalfLog2e), cu.w);
+    // this lane's two consecutive list entries (a, b) = (64 b + 2 lane, 64 b + 2 lane + 1)
+    const int ja = 64 * b + 2 * lane, jb = ja + 1;
+    float2 xya = make_float2(0.f, 0.f), xyb = xya;
+    float4 cua = make_float4(0.f, 0.f, 0.f, 0.f), cub = cua, ca = cua, cb = cua;
+    if (ja < n) {
+      const uint32_t r = vals[rg.x + ja];
+      xya = mean2d[r];
+      cua = conic_o[r];
+      ca = rgb[r];
+    }
+    if (jb < n) {
+      const uint32_t r = vals[rg.x + jb];
+      xyb = mean2d[r];
+      cub = conic_o[r];
+      cb = rgb[r];
     }
     int nl = 0;
     for (int p0 = 0; p0 < NP; p0 += 32) {
       const int p = p0 + lane;
-      const bool on = s_stop[p] > (uint32_t)(32 * b);
+      const bool on = s_stop[p] > (uint32_t)(64 * b);
       const uint32_t bal = __ballot_sync(0xffffffffu, on);
       if (on) live[nl + __popc(bal & lt)] = (uint16_t)p;
       nl += __popc(bal);
     }
     __syncwarp();
-    const int npair = (nl + 1) >> 1;
+    // the checkpoint slot of each 8 x 8 block at the bucket's first position (the
+    // forward's 32-entry step 2 b; lane k holds block k's); a block holding a live pixel
+    // was walked by its forward warp, so its entry is current
     uint32_t bslot = kCkptNone;
-    if (lane < NB) bslot = ckpt.table[(bk0 + (uint64_t)b) * NB + lane];
-    // the pair `pair` for this lane: pixel indices (-1 past the list) and checkpoints
-    int pa = -1, pb = -1;
-    float4 ka = make_float4(1.f, 0.f, 0.f, 0.f), kb = ka;
-    auto pix_ckpt = [&](int pn) {
+    if (lane < NB) bslot = ckpt.table[(bk0 + 2 * (uint64_t)b) * NB + lane];
+    // live pixel `slot` for this lane: its index (-1 past the list) and checkpoint
+    int pn = -1;
+    float4 kn = make_float4(1.f, 0.f, 0.f, 0.f);
+    auto fetch = [&](int slot) {
+      pn = slot < nl ? (int)live[slot] : -1;
       const int px = pn & (TW - 1), py = pn / TW;
       const uint32_t sl = __shfl_sync(0xffffffffu, bslot, (py >> 3) * (TW / 8) + (px >> 3));
-      float4 k = make_float4(1.f, 0.f, 0.f, 0.f);
-      if (pn >= 0 && sl != kCkptNone) k = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
-      return k;
-    };
-    auto fetch = [&](int pair) {
-      pa = 2 * pair < nl ? (int)live[2 * pair] : -1;
-      pb = 2 * pair + 1 < nl ? (int)live[2 * pair + 1] : -1;
-      ka = pix_ckpt(pa);
-      kb = pix_ckpt(pb);
+      kn = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (pn >= 0 && sl != kCkptNone) kn = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
     };
     fetch(lane);
-    // ring slots 32..63 read as stopped pairs until the second chunk replaces them
-    r0[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r1[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r2[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r3[32 + lane] = make_float4(1.f, 1.f, 0.f, 0.f);
-    // moments accumulated negated (see dLda below), colour terms as they are; each a
-    // (pixel a, pixel b) pair summed in the epilogue
+    // ring slots 32..63 read as stopped until the second chunk replaces them
+    ra[32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rb[32 + lane] = make_float4(0.f, 0.f, 1.f, 0.f);
+    // moments accumulated negated (see nd below), colour terms as they are; .x the
+    // sums of entry a, .y of entry b
     float2 v0 = f2(0.f), v1 = f2(0.f), v2 = f2(0.f), v3 = f2(0.f), v4 = f2(0.f), v5 = f2(0.f);
     float2 v6 = f2(0.f), v7 = f2(0.f), v8 = f2(0.f);
-    float2 T = f2(1.f), Rr = f2(0.f);
-    const uint32_t jj = (uint32_t)j;
-    const float2 U = f2(xy.x), V = f2(xy.y), A2 = f2(co.x), BE = f2(co.y), G2 = f2(co.z), O = f2(co.w);
-    const float2 NCX = f2(-c.x), NCY = f2(-c.y), NCZ = f2(-c.z);
-    for (int s0 = 0; s0 < npair + 31; s0 += 32) {
+    float T = 1.f, Rr = 0.f;
+    const uint32_t jja = (uint32_t)ja, jjb = (uint32_t)jb;
+    const float2 U = f2(xya.x, xyb.x), V = f2(xya.y, xyb.y);
+    const float2 A2 = f2(__fmul_rn(cua.x, kNegHalfLog2e), __fmul_rn(cub.x, kNegHalfLog2e));
+    const float2 BE = f2(cua.y, cub.y);
+    const float2 G2 = f2(__fmul_rn(cua.z, kNegHalfLog2e), __fmul_rn(cub.z, kNegHalfLog2e));
+    const float2 O = f2(cua.w, cub.w);
+    const float2 NCX = f2(-ca.x, -cb.x), NCY = f2(-ca.y, -cb.y), NCZ = f2(-ca.z, -cb.z);
+    for (int s0 = 0; s0 < nl + 31; s0 += 32) {
       {
-        // ring slots s0 .. s0 + 31; a pixel past the list reads as stopped (stop 0)
-        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
-        uint32_t sa = 0, sb = 0;
-        float xa = 0.f, ya = 0.f, xb = 0.f, yb = 0.f, ta = 1.f, tb = 1.f, ra_ = 0.f, rb_ = 0.f;
-        if (pa >= 0) {
-          ga = s_g[pa];
-          sa = s_stop[pa];
-          xa = (float)(tc.tx * TW + pa % TW) + 0.5f;
-          ya = (float)(tc.ty * TH + pa / TW) + 0.5f;
-          ta = ka.x;
-          ra_ = ga.w - (ka.y * ga.x + ka.z * ga.y + ka.w * ga.z);
+        // ring slots s0 .. s0 + 31; past the list a slot reads as stopped (stop 0)
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (pn >= 0) {
+          const float4 g = s_g[pn];
+          A = make_float4(g.x, g.y, g.z, __uint_as_float(s_stop[pn]));
+          B = make_float4((float)(tc.tx * TW + pn % TW) + 0.5f, (float)(tc.ty * TH + pn / TW) + 0.5f, kn.x,
+                          g.w - (kn.y * g.x + kn.z * g.y + kn.w * g.z));
         }
-        if (pb >= 0) {
-          gb = s_g[pb];
-          sb = s_stop[pb];
-          xb = (float)(tc.tx * TW + pb % TW) + 0.5f;
-          yb = (float)(tc.ty * TH + pb / TW) + 0.5f;
-          tb = kb.x;
-          rb_ = gb.w - (kb.y * gb.x + kb.z * gb.y + kb.w * gb.z);
-        }
-        const int slot = (s0 + lane) & (kSplatRing - 1);
-        r0[slot] = make_float4(ga.x, gb.x, ga.y, gb.y);
-        r1[slot] = make_float4(ga.z, gb.z, __uint_as_float(sa), __uint_as_float(sb));
-        r2[slot] = make_float4(xa, xb, ya, yb);
-        r3[slot] = make_float4(ta, tb, ra_, rb_);
+        ra[(s0 + lane) & (kSplatRing - 1)] = A;
+        rb[(s0 + lane) & (kSplatRing - 1)] = B;
         fetch(s0 + 32 + lane);
         __syncwarp();
       }
-      const int s1 = min(s0 + 32, npair + 31);
-      const float4 *rw = s_ring[warp][0];
+      const int s1 = min(s0 + 32, nl + 31);
 #pragma unroll 4
       for (int s = s0; s < s1; ++s) {
         const float4 *q = rw + ((s - lane) & (kSplatRing - 1));
-        const float Ta = __shfl_up_sync(0xffffffffu, T.x, 1), Tb = __shfl_up_sync(0xffffffffu, T.y, 1);
-        const float Ra = __shfl_up_sync(0xffffffffu, Rr.x, 1), Rb = __shfl_up_sync(0xffffffffu, Rr.y, 1);
-        const float4 q0 = q[0], q1 = q[kSplatRing], q2 = q[2 * kSplatRing], q3 = q[3 * kSplatRing];
-        T = lane == 0 ? f2(q3.x, q3.y) : f2(Ta, Tb);
-        Rr = lane == 0 ? f2(q3.z, q3.w) : f2(Ra, Rb);
-        // falloff at both pixels: the forward's operations and roundings
-        const float2 dx = f2_sub(U, f2(q2.x, q2.y)), dy = f2_sub(V, f2(q2.z, q2.w));
+        const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
+        const float Rin = __shfl_up_sync(0xffffffffu, Rr, 1);
+        const float4 g = q[0], p = q[kSplatRing];
+        T = lane == 0 ? p.z : Tin;
+        Rr = lane == 0 ? p.w : Rin;
+        // falloff of both entries at this pixel: the forward's operations and roundings
+        const float2 dx = f2_sub(U, f2(p.x)), dy = f2_sub(V, f2(p.y));
         const float2 tt = f2_fma(BE, dy, dx);
         const float2 e = f2_fma(f2_mul(A2, tt), tt, f2_mul(G2, f2_mul(dy, dy)));
         const float2 G = f2(ex2_approx(e.x), ex2_approx(e.y));
         const float2 raw = f2_mul(O, G);
         const float2 al = f2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
         // a position before the pixel's stop (false on stopped pixels and for lanes
-        // without an entry) where sigma reaches the floor; elsewhere the pixel gets
-        // sigma 0: T, R and every sum stay as they are
-        const bool oka = jj < __float_as_uint(q1.z) && al.x >= kAlphaMin;
-        const bool okb = jj < __float_as_uint(q1.w) && al.y >= kAlphaMin;
-        const float2 ae = f2(oka ? al.x : 0.f, okb ? al.y : 0.f);
-        const float2 one_m = f2_sub(f2(1.f), ae);
-        const float2 w = f2_mul(ae, T);
-        const float2 gx = f2(q0.x, q0.y), gy = f2(q0.z, q0.w), gz = f2(q1.x, q1.y);
-        const float2 ncd = f2_fma(NCZ, gz, f2_fma(NCY, gy, f2_mul(NCX, gx)));   // -<c, g>
-        Rr = f2_fma(ncd, w, Rr);
-        // -dL/dsigma = -T <c, g> + R / (1 - sigma)
-        const float2 nd = f2_fma(T, ncd, f2_mul(Rr, f2(rcp_approx(one_m.x), rcp_approx(one_m.y))));
-        T = f2_mul(T, one_m);
-        v6 = f2_fma(gx, w, v6);
-        v7 = f2_fma(gy, w, v7);
-        v8 = f2_fma(gz, w, v8);
-        const float2 mg = f2_mul(nd, G);
+        // without an entry) where sigma reaches the floor; elsewhere sigma 0 leaves T,
+        // R and every sum as they are
+        const uint32_t stop = __float_as_uint(g.w);
+        const bool oka = jja < stop && al.x >= kAlphaMin, okb = jjb < stop && al.y >= kAlphaMin;
+        const float2 ncd = f2_fma(NCZ, f2(g.z), f2_fma(NCY, f2(g.y), f2_mul(NCX, f2(g.x))));   // -<c, g>
+        // entry a, then entry b, in list order: -dL/dsigma = -T <c, g> + R / (1 - sigma)
+        const float sa = oka ? al.x : 0.f;
+        const float oma = __fsub_rn(1.f, sa);
+        const float wa = sa * T;
+        Rr = fmaf(ncd.x, wa, Rr);
+        const float nda = fmaf(T, ncd.x, Rr * rcp_approx(oma));
+        T = __fmul_rn(T, oma);
+        const float sb = okb ? al.y : 0.f;
+        const float omb = __fsub_rn(1.f, sb);
+        const float wb = sb * T;
+        Rr = fmaf(ncd.y, wb, Rr);
+        const float ndb = fmaf(T, ncd.y, Rr * rcp_approx(omb));
+        T = __fmul_rn(T, omb);
+        const float2 w = f2(wa, wb);
+        v6 = f2_fma(f2(g.x), w, v6);
+        v7 = f2_fma(f2(g.y), w, v7);
+        v8 = f2_fma(f2(g.z), w, v8);
+        const float2 mg = f2_mul(f2(nda, ndb), G);
         const float2 m = f2(oka && raw.x <= kAlphaMax ? mg.x : 0.f, okb && raw.y <= kAlphaMax ? mg.y : 0.f);
         const float2 mt = f2_mul(m, tt), mdy = f2_mul(m, dy);
         v0 = f2_add(v0, mt);
@@ -874,14 +865,22 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
       }
       __syncwarp();   // this chunk's reads before the next chunk's ring writes
     }
-    const float v[9] = {-(v0.x + v0.y), -(v1.x + v1.y), -(v2.x + v2.y), -(v3.x + v3.y), -(v4.x + v4.y),
-                        -(v5.x + v5.y), v6.x + v6.y, v7.x + v7.y, v8.x + v8.y};
-    if (has && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f || v[5] != 0.f ||
-                v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
-      const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
-      red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
-      red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
-      red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
+    // each entry's sums once into its record's gradients (record and conic read again)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jh = h == 0 ? ja : jb;
+      const float v[9] = {-(h == 0 ? v0.x : v0.y), -(h == 0 ? v1.x : v1.y), -(h == 0 ? v2.x : v2.y),
+                          -(h == 0 ? v3.x : v3.y), -(h == 0 ? v4.x : v4.y), -(h == 0 ? v5.x : v5.y),
+                          h == 0 ? v6.x : v6.y, h == 0 ? v7.x : v7.y, h == 0 ? v8.x : v8.y};
+      if (jh < n && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f ||
+                     v[5] != 0.f || v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
+        const uint32_t r = vals[rg.x + jh];
+        const float4 cu = conic_o[r];
+        const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
+        red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
+        red_add_v4(g_co + 4 * (size_t)r, ho * v[2], -oA * v[3], ho * v[4], v[5]);
+        red_add_v4(g_rgb + 4 * (size_t)r, v[6], v[7], v[8], 0.f);
+      }
     }
     __syncwarp();   // the next bucket rewrites this warp's live list
     uint32_t nxt = 0;
