@@ -401,6 +401,16 @@ gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_params_t *in,
                              int64_t out_capacity, int64_t *d_new_n, int32_t *d_error,
                              void *ws, size_t ws_bytes, gs_stream_t stream);
 
+/* Debug builds (libgs_debug.so, compiled with -DGS_DEBUG): the hot path checks its
+ * index accesses (record ids from the lists, the lists' ranges, checkpoint table
+ * entries and slots, list positions) before making them; a failed check is recorded
+ * and the access skipped. gs_debug_status returns the first failure since the last
+ * call as (code << 48 | index), 0 if none, and clears it (synchronising the device).
+ * Codes: 1 record id >= records, 2 tile range outside the list, 3 checkpoint table
+ * index or slot out of range, 4 list position >= capacity. The release library
+ * returns GS_ERR_UNSUPPORTED (and 0). */
+gs_status_t gs_debug_status(uint64_t *word);
+
 /* ------------------------------------------------------------ training step */
 /* Eq. 3: L = (1 - lambda) ||I - I_hat||_1 + lambda D-SSIM(I, I_hat), per view: the L1
  * term as the mean over 3 H W values, D-SSIM = 1 - SSIM with SSIM averaged over the

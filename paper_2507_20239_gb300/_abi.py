@@ -119,6 +119,7 @@ SIGNATURES = {
     "gs_downscale": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]),
     "gs_spectrum_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "gs_spectrum_l1": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_size_t, vp]),
+    "gs_debug_status": (C.c_int, [P(C.c_uint64)]),
 }
 
 _lib = None

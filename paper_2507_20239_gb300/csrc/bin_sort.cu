@@ -32,6 +32,10 @@
 
 namespace gs {
 
+#ifdef GS_DEBUG
+GS_DEBUG_TAKE(debug_take_bin_sort)
+#endif
+
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsItems = 8;
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
                                                        int64_t n_per_view, int tw, int th, int fbits,
                                                        uint32_t *__restrict__ hist, BinRec *__restrict__ brec,
                                                        uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
-                                                       uint32_t *work) {
+                                                       uint32_t *work, uint64_t cap) {
   __shared__ BinRec s_rec[8][32];
   __shared__ uint2 s_unit[8][kUnits];            // (record slot << 24 | run length, tile id of the run's first column)
   __shared__ uint32_t s_hpre[8][kUnits + 1];     // exclusive scan of the run lengths
@@ -444,8 +448,10 @@ __global__ void __launch_bounds__(256) bin_rows_kernel(gs_proj_t P, const uint32
           __syncwarp();
           if (hit) {
             const uint32_t pos = cur + __popc(peers & lt);
-            dkeys[pos] = tile;
-            dvals[pos] = r;
+            if (GS_CHECK(pos < cap, 4, pos)) {
+              dkeys[pos] = tile;
+              dvals[pos] = r;
+            }
             if ((peers & lt) == 0) s_cur[wib][dig] = cur + __popc(peers);
           }
           __syncwarp();
@@ -660,7 +666,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const int eg = num_sms() * 8;
   bin_rows_kernel<false><<<eg, 256, 0, s>>>(*proj, order, n_vis, nullptr, frame->cams_dev, frame->n_views,
                                               n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
-                                              nullptr, nullptr, w.counters + 3);
+                                              nullptr, nullptr, w.counters + 3, (uint64_t)bins->capacity);
   GS_LAUNCH_CHECK();
   HistScan hs{w.dhist, n_vis, fbits, (uint64_t)bins->capacity, m_total, overflow, bins->d_count, d_error};
   if (gs_status_t st = run_scan(hs, w.block_sums, G, s)) return st;
@@ -671,7 +677,8 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   const bool emit_to_A = (passes % 2) == 0;
   bin_rows_kernel<true><<<eg, 256, 0, s>>>(*proj, order, n_vis, overflow, frame->cams_dev, frame->n_views,
                                              n_per_view, frame->tile_w, frame->tile_h, fbits, w.dhist, w.brec,
-                                             emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v, w.counters + 4);
+                                             emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v, w.counters + 4,
+                                             (uint64_t)bins->capacity);
   GS_LAUNCH_CHECK();
   // 5. stable sort by the remaining tile-id bits
   bool res0 = true;

@@ -56,3 +56,18 @@ extern "C" gs_status_t gs_frame_init(gs_camera_t *cams, int32_t n_views, int32_t
   frame->max_height = mh;
   return GS_OK;
 }
+
+// The first failed bounds check of a debug build since the last call, as
+// (code << 48 | index), 0 if none; clears it. Release builds: GS_ERR_UNSUPPORTED.
+extern "C" gs_status_t gs_debug_status(uint64_t *word) {
+  if (!word) return GS_ERR_INVALID_ARG;
+  *word = 0;
+#ifdef GS_DEBUG
+  const uint64_t a = gs::debug_take_raster(), b = gs::debug_take_bin_sort();
+  if (a == ~0ull || b == ~0ull) return GS_ERR_CUDA;
+  *word = a ? a : b;
+  return GS_OK;
+#else
+  return GS_ERR_UNSUPPORTED;
+#endif
+}

@@ -25,6 +25,35 @@ void count_launch();
 
 namespace gs {
 
+// Debug builds (-DGS_DEBUG, libgs_debug.so): the hot path's index accesses (record
+// ids read from the tile lists, the lists' ranges, checkpoint table entries and
+// slots, the emitted list positions) are checked before they are made. A failed check
+// records (code << 48 | index) in the translation unit's debug word, the first failure
+// winning, and the access is skipped, so the launch completes and gs_debug_status
+// reports what went wrong. Release builds compile every check to `true`.
+// Codes: 1 record id >= records, 2 tile range outside the list, 3 checkpoint table
+// index or slot out of range, 4 list position >= capacity.
+#ifdef GS_DEBUG
+static __device__ unsigned long long g_gs_debug_word;
+__device__ __forceinline__ bool debug_check(bool ok, uint32_t code, uint64_t index) {
+  if (!ok) atomicCAS(&g_gs_debug_word, 0ull, ((unsigned long long)code << 48) | (index & 0xffffffffffffull));
+  return ok;
+}
+#define GS_CHECK(cond, code, index) ::gs::debug_check((cond), (code), (uint64_t)(index))
+// Host side of a translation unit's word: read and clear it (synchronising).
+#define GS_DEBUG_TAKE(fn)                                                          \
+  uint64_t fn() {                                                                \
+    unsigned long long v = 0, z = 0;                                             \
+    if (cudaMemcpyFromSymbol(&v, g_gs_debug_word, sizeof(v)) != cudaSuccess) return ~0ull; \
+    if (cudaMemcpyToSymbol(g_gs_debug_word, &z, sizeof(z)) != cudaSuccess) return ~0ull;   \
+    return v;                                                                    \
+  }
+uint64_t debug_take_raster();
+uint64_t debug_take_bin_sort();
+#else
+#define GS_CHECK(cond, code, index) true
+#endif
+
 constexpr float kNear = 0.2f;            // default near plane (the camera carries its own)
 constexpr float kDilation = 0.3f;        // low-pass dilation added to the 2D covariance (px^2)
 constexpr float kFovClamp = 1.3f;        // J is evaluated with t_x/t_z clamped to +-1.3 (W/2)/f

@@ -23,6 +23,10 @@
 
 namespace gs {
 
+#ifdef GS_DEBUG
+GS_DEBUG_TAKE(debug_take_raster)
+#endif
+
 struct TileCoord {
   int view, tx, ty, W, H;
   int64_t pix_off;
@@ -181,6 +185,7 @@ struct FwdArgs {
   float *__restrict__ T_final;
   uint32_t *__restrict__ stop_out;
   CkptLayout ckpt;
+  uint64_t n_records, list_cap;   // bounds of the record ids and list positions (debug checks)
 };
 
 // One warp's 8 x 8 block `warp` of `tile`, with the warp's staging slots.
@@ -208,14 +213,15 @@ __device__ __forceinline__ void fwd_warp_block(const FwdArgs &a, int tile, int w
   float2 T = f2(1.f), cr = f2(0.f), cg = f2(0.f), cb = f2(0.f);   // (pixel 0, pixel 1)
   uint32_t st0 = 0, st1 = 0;
   bool done0 = !in0, done1 = !in1;
-  const uint2 rg = a.ranges[tile];
+  uint2 rg = a.ranges[tile];
+  if (!GS_CHECK(rg.x <= rg.y && (uint64_t)rg.y <= a.list_cap, 2, tile)) rg = make_uint2(0u, 0u);
   const int n = (int)(rg.y - rg.x);
   // software pipeline: the record id two steps ahead, the record one step ahead
   uint32_t r_next = lane < n ? vals[rg.x + lane] : 0u;
   uint32_t r_next2 = 32 + lane < n ? vals[rg.x + 32 + lane] : 0u;
   float2 xy_n = make_float2(0.f, 0.f);
   float4 co_n = make_float4(0.f, 0.f, 0.f, 0.f), c_n = co_n;
-  if (lane < n) {
+  if (lane < n && GS_CHECK(r_next < a.n_records, 1, r_next)) {
     xy_n = mean2d[r_next];
     co_n = conic_o[r_next];
     c_n = rgb[r_next];
@@ -238,11 +244,11 @@ __device__ __forceinline__ void fwd_warp_block(const FwdArgs &a, int tile, int w
         const uint64_t idx = (ckpt_bucket(rg.x, tile) + (uint64_t)(base >> 5)) * NW + warp;
         if (ckpt.n_slots >= ckpt.table_entries) slot = (uint32_t)idx;      // room for every pair
         else if (claim < ckpt.pool_size) slot = (uint32_t)(pool * ckpt.pool_size + claim);
-        ckpt.table[idx] = slot;
+        if (GS_CHECK(idx < ckpt.table_entries, 3, idx)) ckpt.table[idx] = slot;
         if (base + 64 < n) claim = atomicAdd(ckpt.pools + pool, 1u);
       }
       slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (slot != kCkptNone) {
+      if (slot != kCkptNone && GS_CHECK(slot < ckpt.n_slots, 3, slot)) {
         float4 *ck = ckpt.slots + (uint64_t)slot * 64 + (lane >> 2) * 8 + 2 * (lane & 3);
         if (!done0) ck[0] = make_float4(T.x, cr.x, cg.x, cb.x);
         if (!done1) ck[1] = make_float4(T.y, cr.y, cg.y, cb.y);
@@ -253,7 +259,7 @@ __device__ __forceinline__ void fwd_warp_block(const FwdArgs &a, int tile, int w
     const float4 co = co_n, c = c_n;
     // issue the next step's gathers and the id after it before compositing this one
     r_next = r_next2;
-    if (j + 32 < n) {
+    if (j + 32 < n && GS_CHECK(r_next < a.n_records, 1, r_next)) {
       xy_n = mean2d[r_next];
       co_n = conic_o[r_next];
       c_n = rgb[r_next];
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
     const float2 *__restrict__ mean2d, const float4 *__restrict__ conic_o, const float4 *__restrict__ rgb,
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, float bg0, float bg1, float bg2, float *__restrict__ image, float *__restrict__ T_final,
-    uint32_t *__restrict__ stop_out, uint32_t *__restrict__ counts) {
+    uint32_t *__restrict__ stop_out, uint32_t *__restrict__ counts, uint64_t n_records, uint64_t list_cap) {
   constexpr int NT = TW * TH / 2;
   static_assert(NT <= 256, "list positions are bytes");
   __shared__ float2 s_xy[NT];
@@ -379,14 +385,17 @@ __global__ void __launch_bounds__(TW *TH / 2) raster_fwd_kernel(
   uint32_t st0 = 0, st1 = 0;
   uint32_t ex0 = 0, ex1 = 0, nc0 = 0, nc1 = 0;
   bool done0 = !in0, done1 = !in1;
-  const uint2 rg = ranges[blockIdx.x];
+  uint2 rg = ranges[blockIdx.x];
+  if (!GS_CHECK(rg.x <= rg.y && (uint64_t)rg.y <= list_cap, 2, blockIdx.x)) rg = make_uint2(0u, 0u);
   const int n = (int)(rg.y - rg.x);
   for (int base = 0; base < n; base += NT) {
     if (__syncthreads_count(!(done0 && done1)) == 0) break;
     if (base + t < n) {
       float4 co_raw;
-      stage<TW, TH, 8, 8>(mean2d, conic_o, rgb, vals[rg.x + base + t], tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t],
-                          s_co[t], s_rgb[t], co_raw);
+      const uint32_t r = vals[rg.x + base + t];
+      if (GS_CHECK(r < n_records, 1, r))
+        stage<TW, TH, 8, 8>(mean2d, conic_o, rgb, r, tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t],
+                            s_rgb[t], co_raw);
     }
     __syncthreads();
     if (__all_sync(0xffffffffu, done0 && done1)) continue;
@@ -549,7 +558,7 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
     const uint32_t *__restrict__ stop_in, float *__restrict__ g_mean2d, float *__restrict__ g_co,
-    float *__restrict__ g_rgb) {
+    float *__restrict__ g_rgb, uint64_t n_records, uint64_t list_cap) {
   constexpr int NT = TW * TH / PX, CH = HALF ? NT / 2 : NT, BW = 8, BH = 4 * PX;
   __shared__ float2 s_xy[CH];
   __shared__ float4 s_co[CH];
@@ -587,7 +596,8 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     for (int k = 0; k < PX; ++k) d = d && q[k].done;
     return d;
   };
-  const uint2 rg = ranges[blockIdx.x];
+  uint2 rg = ranges[blockIdx.x];
+  if (!GS_CHECK(rg.x <= rg.y && (uint64_t)rg.y <= list_cap, 2, blockIdx.x)) rg = make_uint2(0u, 0u);
   int n = (int)(rg.y - rg.x);
   uint32_t wstop = 0;
   if (STOP) {
@@ -610,7 +620,8 @@ __global__ void __launch_bounds__(TW *TH / PX) raster_bwd_kernel(
     }
     const int cnt = min(CH, n - base);
     if (t < cnt) {
-      const uint32_t r = vals[rg.x + base + t];
+      uint32_t r = vals[rg.x + base + t];
+      if (!GS_CHECK(r < n_records, 1, r)) r = 0;
       s_rec[t] = r;
       stage<TW, TH, BW, BH>(mean2d, conic_o, rgb, r, tc.tx * TW, tc.ty * TH, tc.W, tc.H, s_xy[t], s_co[t], s_rgb[t],
                             s_cu[t]);
@@ -693,7 +704,7 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
     const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, const gs_camera_t *__restrict__ cams,
     int n_views, const float *__restrict__ image, const float *__restrict__ d_image,
     const uint32_t *__restrict__ stop_in, const CkptLayout ckpt, float *__restrict__ g_mean2d,
-    float *__restrict__ g_co, float *__restrict__ g_rgb) {
+    float *__restrict__ g_co, float *__restrict__ g_rgb, uint64_t n_records, uint64_t list_cap) {
   constexpr int NP = TW * TH, NW = kSplatThreads / 32, NB = TW * TH / 64;
   static_assert(NP % 32 == 0 && NP <= 65536, "whole warps of pixels, 16-bit indices");
   __shared__ float4 s_g[NP];                       // (dL/dout, <out, dL/dout>)
@@ -735,7 +746,8 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
     if (lane == 0) atomicMax(&s_max, mx);
   }
   __syncthreads();
-  const uint2 rg = ranges[tile];
+  uint2 rg = ranges[tile];
+  if (!GS_CHECK(rg.x <= rg.y && (uint64_t)rg.y <= list_cap, 2, tile)) rg = make_uint2(0u, 0u);
   const int n = min((int)(rg.y - rg.x), (int)s_max);
   const int nb = (n + 63) >> 6;                     // buckets of 64 list entries
   const uint64_t bk0 = ckpt_bucket(rg.x, tile);
@@ -749,15 +761,19 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
     float4 cua = make_float4(0.f, 0.f, 0.f, 0.f), cub = cua, ca = cua, cb = cua;
     if (ja < n) {
       const uint32_t r = vals[rg.x + ja];
-      xya = mean2d[r];
-      cua = conic_o[r];
-      ca = rgb[r];
+      if (GS_CHECK(r < n_records, 1, r)) {
+        xya = mean2d[r];
+        cua = conic_o[r];
+        ca = rgb[r];
+      }
     }
     if (jb < n) {
       const uint32_t r = vals[rg.x + jb];
-      xyb = mean2d[r];
-      cub = conic_o[r];
-      cb = rgb[r];
+      if (GS_CHECK(r < n_records, 1, r)) {
+        xyb = mean2d[r];
+        cub = conic_o[r];
+        cb = rgb[r];
+      }
     }
     int nl = 0;
     for (int p0 = 0; p0 < NP; p0 += 32) {
@@ -772,7 +788,10 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
     // forward's 32-entry step 2 b; lane k holds block k's); a block holding a live pixel
     // was walked by its forward warp, so its entry is current
     uint32_t bslot = kCkptNone;
-    if (lane < NB) bslot = ckpt.table[(bk0 + 2 * (uint64_t)b) * NB + lane];
+    if (lane < NB) {
+      const uint64_t ti = (bk0 + 2 * (uint64_t)b) * NB + lane;
+      if (GS_CHECK(ti < ckpt.table_entries, 3, ti)) bslot = ckpt.table[ti];
+    }
     // live pixel `slot` for this lane: its index (-1 past the list) and checkpoint
     int pn = -1;
     float4 kn = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -781,7 +800,8 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
       const int px = pn & (TW - 1), py = pn / TW;
       const uint32_t sl = __shfl_sync(0xffffffffu, bslot, (py >> 3) * (TW / 8) + (px >> 3));
       kn = make_float4(1.f, 0.f, 0.f, 0.f);
-      if (pn >= 0 && sl != kCkptNone) kn = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
+      if (pn >= 0 && sl != kCkptNone && GS_CHECK(sl < ckpt.n_slots, 3, sl))
+        kn = ckpt.slots[(uint64_t)sl * 64 + (py & 7) * 8 + (px & 7)];
     };
     fetch(lane);
     // ring slots 32..63 read as stopped until the second chunk replaces them
@@ -875,6 +895,7 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
       if (jh < n && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f || v[4] != 0.f ||
                      v[5] != 0.f || v[6] != 0.f || v[7] != 0.f || v[8] != 0.f)) {
         const uint32_t r = vals[rg.x + jh];
+        if (!GS_CHECK(r < n_records, 1, r)) continue;
         const float4 cu = conic_o[r];
         const float oA = cu.w * cu.x, ho = -0.5f * cu.w;
         red_add_v2(g_mean2d + 2 * (size_t)r, -oA * v[0], -(oA * cu.y * v[0] + cu.w * cu.z * v[1]));
@@ -934,6 +955,8 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
     a.T_final = T_final;
     a.stop_out = cfg->store_stop ? stop : nullptr;
     a.ckpt = ckpt ? *ckpt : CkptLayout{};
+    a.n_records = (uint64_t)proj->n_records;
+    a.list_cap = (uint64_t)bins->capacity;
     if (cfg->d_queue) {
       // persistent grid: every CTA the SMs hold at once
       GS_CUDA_TRY(cudaMemsetAsync(cfg->d_queue, 0, sizeof(uint32_t), s));
@@ -953,7 +976,7 @@ static gs_status_t launch_fwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
       frame->cams_dev, frame->n_views, cfg->bg[0], cfg->bg[1], cfg->bg[2], image, T_final,
-      cfg->store_stop ? stop : nullptr, counts);
+      cfg->store_stop ? stop : nullptr, counts, (uint64_t)proj->n_records, (uint64_t)bins->capacity);
   GS_LAUNCH_CHECK();
   return GS_OK;
 }
@@ -976,7 +999,7 @@ static gs_status_t launch_bwd(const gs_proj_t *proj, const gs_bins_t *bins, cons
 #define GS_BWD(STOPV, HALFV)                                                                               \
   raster_bwd_kernel<TW, TH, PX, STOPV, HALFV><<<frame->n_tiles, TW * TH / PX, 0, s>>>(                       \
       m2, co, c, bins->vals, rg, frame->cams_dev, frame->n_views, image, d_image, stop, g->d_mean2d,          \
-      g->d_conic_opacity, g->d_rgb)
+      g->d_conic_opacity, g->d_rgb, (uint64_t)proj->n_records, (uint64_t)bins->capacity)
   if (stop)
     half ? GS_BWD(true, true) : GS_BWD(true, false);
   else
@@ -997,7 +1020,8 @@ static gs_status_t launch_bwd_splat(const gs_proj_t *proj, const gs_bins_t *bins
   raster_bwd_splat_kernel<TW, TH><<<frame->n_tiles * kSplatSplit, kSplatThreads, 0, s>>>(
       reinterpret_cast<const float2 *>(proj->mean2d), reinterpret_cast<const float4 *>(proj->conic_opacity),
       reinterpret_cast<const float4 *>(proj->rgb), bins->vals, reinterpret_cast<const uint2 *>(bins->ranges),
-      frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb);
+      frame->cams_dev, frame->n_views, image, d_image, stop, ckpt, g->d_mean2d, g->d_conic_opacity, g->d_rgb,
+      (uint64_t)proj->n_records, (uint64_t)bins->capacity);
   GS_LAUNCH_CHECK();
   return GS_OK;
 }

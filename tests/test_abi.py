@@ -157,3 +157,15 @@ def test_checkpoint_size_and_bucket_layout(lib):
                 k = int(starts[t]) // 32 + t + b
                 assert k not in used and k < (M + 31) // 32 + n_tiles, (trial, t, b)
                 used.add(k)
+
+
+def test_debug_status_entry_point(lib):
+    # the release library has no bounds checks compiled in and says so; the debug
+    # library (-DGS_DEBUG) builds and exports the same entry points
+    import ctypes as C
+    w = C.c_uint64(5)
+    assert lib.gs_debug_status(C.byref(w)) == 5 and w.value == 0      # GS_ERR_UNSUPPORTED
+    assert lib.gs_debug_status(None) == 1
+    dbg = _abi.load(gbuild.build(debug=True))
+    missing = [n for n in declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
