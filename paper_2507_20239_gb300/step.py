@@ -61,16 +61,6 @@ def duplicates(params: dict, sh_degree: int, frame: R.Frame) -> int:
     return int(bins.count.item())
 
 
-def ckpt_slots(params: dict, sh_degree: int, frame: R.Frame, capacity: int) -> int:
-    """Checkpoint slots the per-splat forward needs for these parameters on this frame
-    (one projection, binning and forward into a buffer without slots, synchronising)."""
-    proj = R.project(params, sh_degree, frame)
-    bins = R.bin_sort(proj, frame, capacity=capacity)
-    ck = R.alloc_ckpt(frame, bins, 0)
-    R.raster_fwd_ckpt(proj, bins, frame, ck)
-    return int(R.ckpt_usage(frame, bins, ck)[0].item())
-
-
 class TrainStep:
     def __init__(self, params: dict, sh_degree: int, cameras, target_images, config: StepConfig = StepConfig(),
                  device="cuda", capacity: int | None = None, headroom: float = 1.25, store_stop: bool = True,
@@ -92,11 +82,20 @@ class TrainStep:
         self.ckpt = None
         if self.splat:
             # checkpoint slots for the (bucket, block) pairs the forward walks, measured
-            # with headroom (-1: one per possible pair)
-            if slots is None:
-                slots = int(ckpt_slots(params, sh_degree, f, capacity) * headroom) + 4 * 256
-            self.ckpt = R.alloc_ckpt(f, self.bins, slots)
+            # on the step's own buffers (a forward into a checkpoint buffer without
+            # slots reports the count), reserved with headroom; -1: one per possible pair
             self.ckpt_use = torch.zeros(2, dtype=torch.int64, device=f.device)
+            if slots is None:
+                probe = R.alloc_ckpt(f, self.bins, 0)
+                R.project(params, sh_degree, f, out=self.proj)
+                R.bin_sort_into(self.proj, f, self.bins)
+                R.raster_fwd_ckpt(self.proj, self.bins, f, probe, image=self.image, T_final=self.T, stop=self.stop)
+                R.ckpt_usage(f, self.bins, probe, out=self.ckpt_use)
+                if int(self.bins.error.item()) != 0:
+                    raise RuntimeError("TrainStep: duplicate capacity exceeded while sizing the checkpoints")
+                slots = int(int(self.ckpt_use[0].item()) * headroom) + 4 * 256
+                del probe
+            self.ckpt = R.alloc_ckpt(f, self.bins, slots)
         self.queue = torch.zeros(1, dtype=torch.int32, device=f.device) if config.queue else None
         self.d_image = torch.empty_like(self.image)
         self.loss = torch.empty(f.n_views, device=f.device)
