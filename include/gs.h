@@ -189,11 +189,14 @@ gs_status_t gs_project(const gs_params_t *params, const gs_frame_t *frame, gs_pr
                        gs_stream_t stream);
 
 /* Tile binning and depth sort ("tile-based", "depth-sorted"; Sec. "Preliminary").
- * Every visible record is duplicated into each tile of its rectangle; duplicates
- * are ordered by (global tile, FP32 depth bits, record index) and the per-tile
- * ranges written. Device-side: if M > bins->capacity, GS_ERR_CAPACITY is OR-ed into
- * *d_error, *bins->d_count receives the required M and vals/ranges are left
- * empty (every range [0, 0)). */
+ * Every visible record is duplicated into each tile of its rectangle whose box of
+ * pixel centres its footprint ellipse (alpha >= 1/255, with a 0.2% margin) meets;
+ * duplicates are ordered by (global tile, FP32 depth bits, record index) and the
+ * per-tile ranges written. The capacity also holds, while the lists are built, one
+ * entry per tile row of each visible record's rectangle (in practice fewer than M).
+ * Device-side: if M or that row count exceeds bins->capacity, GS_ERR_CAPACITY is
+ * OR-ed into *d_error, *bins->d_count receives the larger of the two (the capacity
+ * needed) and vals holds no lists, every range being [0, 0). */
 gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *frame, gs_bins_t *bins,
                         void *ws, size_t ws_bytes, int32_t *d_error, gs_stream_t stream);
 

@@ -127,10 +127,47 @@ def test_bin_sort_capacity_overflow_reports_and_retries():
     R.bin_sort_into(proj, frame, bins)
     torch.cuda.synchronize()
     assert int(bins.error.item()) == 2                # GS_ERR_CAPACITY
-    assert int(bins.count.item()) == len(vals)        # the required size is reported
+    # the required size is reported: the capacity also holds one entry per tile row
+    # of each visible record's rectangle while the lists are built
+    assert int(bins.count.item()) == max(len(vals), _rect_rows(recs))
     assert np.all(bins.ranges.cpu().numpy() == 0)     # and every list is empty
     # the binding grows the buffer and redoes the sort
     _check(recs, [cam], (16, 16), capacity=len(vals) // 2)
+
+
+def _rect_rows(recs):
+    rows = 0
+    for r in recs:
+        x0, y0, x1, y1 = (r["rect"][:, i].astype(np.int64) for i in range(4))
+        live = (r["radius"] > 0) & (x1 > x0) & (y1 > y0)
+        rows += int(((y1 - y0) * live).sum())
+    return rows
+
+
+def test_bin_sort_rectangle_rows_beyond_the_entry_count():
+    """Tall one-column rectangles around small footprints: the rows the binning
+    visits (13 per record) outnumber the entries (about one per record), so the
+    first capacity (8 entries per record) overflows on the rows alone; the reported
+    size covers them and the retry gives the exact lists."""
+    cam = synth.Camera(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 100., 100., 150., 100., 300, 200)
+    n = 20000
+    recs = _synthetic_records(9, n, [cam], (16, 16))
+    rng = np.random.default_rng(99)
+    r = recs[0]
+    tx, ty = rng.integers(0, 19, n), rng.integers(0, 13, n)
+    r["mean2d"][:] = np.stack([16 * tx + 8, 16 * ty + 8], 1).astype(np.float32)
+    r["conic_f"][:] = [1.0, 0.0, 1.0]
+    r["q_max"][:] = np.float32(2 * np.log(255 * 0.5))
+    r["rect"][:] = np.stack([tx, np.zeros(n), tx + 1, np.full(n, 13)], 1).astype(r["rect"].dtype)
+    r["radius"][:] = 3
+    r["depth"][:] = rng.uniform(1.0, 5.0, n).astype(np.float32)
+    assert _rect_rows(recs) == 13 * n
+    frame = R.Frame([cam])
+    bins = R.alloc_bins(frame, n, capacity=8 * n)
+    R.bin_sort_into(records_to_gpu(recs), frame, bins)
+    torch.cuda.synchronize()
+    assert int(bins.error.item()) == 2 and int(bins.count.item()) == 13 * n
+    assert _check(recs, [cam], (16, 16), capacity=8 * n) == n
 
 
 def test_bin_sort_full_size_orbit_scene():
