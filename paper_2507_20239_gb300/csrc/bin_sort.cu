@@ -420,7 +420,8 @@ __device__ __forceinline__ uint32_t band_columns(float xl, float xr, int x0, int
 // cursor, which starts at the scanned hist entry and advances in (record, row,
 // column) order, so each digit's entries stay in depth order.
 constexpr int kMaxFusedBits = 8;
-constexpr int kUnits = 64;
+constexpr int kCountUnits = 64;    // units per round of the counting pass (two per lane)
+constexpr int kUnits = 128;        // units per round of the emitting pass (four per lane)
 constexpr int kWinCap = 256;   // 32-hit windows per round located by bit masks (else a binary search)
 constexpr uint32_t kRunBits = 24;
 
@@ -486,9 +487,9 @@ __global__ void __launch_bounds__(256) bin_count_kernel(gs_proj_t P, const uint3
     const bool keep = ub + n_units <= unit_cap;
     if (lane == 0) ubatch[batch] = make_uint2(keep ? (uint32_t)ub : 0u, keep ? n_units : 0u);
     __syncwarp();
-    for (uint32_t u0 = 0; u0 < n_units; u0 += kUnits) {
+    for (uint32_t u0 = 0; u0 < n_units; u0 += kCountUnits) {
 #pragma unroll
-      for (int i = 0; i < kUnits / 32; ++i) {
+      for (int i = 0; i < kCountUnits / 32; ++i) {
         const uint32_t u = u0 + lane + 32 * i;
         // owner: the last record j whose rows start at or before u
         int j = 0;
@@ -784,8 +785,7 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
 // w.order[0, n_vis): the visible count and depth range first, then 8-bit passes
 // over the keys (depth bits minus the smallest visible depth's bits), the later ones
 // only while the range needs them (three when the visible depths span less than an
-// octave: 24 bits). The
-// first pass compacts the visible records as it sorts.
+// octave: 24 bits). The first pass compacts the visible records as it sorts.
 static gs_status_t depth_sort(const gs_proj_t *proj, int64_t R, const BinWs &w, uint32_t *n_vis,
                               uint32_t *range, cudaStream_t s) {
   const int G = radix_blocks();
