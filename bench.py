@@ -194,8 +194,9 @@ def measure_capacity(sc, frame, P):
 
 def splat_bucket_stats(step):
     """Work of the per-splat backward on view 0 from the forward's stop indices:
-    32-entry buckets walked (per tile, up to its largest stop index) and live
-    (pixel, bucket) pairs (per pixel, ceil(stop / 32))."""
+    64-entry buckets walked (per tile, up to its largest stop index) and live
+    (pixel, bucket) pairs (per pixel, ceil(stop / 64)); a bucket takes its live
+    pixels + 31 warp steps."""
     import torch
     if step.stop is None:
         return None
@@ -207,8 +208,8 @@ def splat_bucket_stats(step):
     pad = torch.zeros(gy * th, gx * tw, dtype=torch.int64, device=st.device)
     pad[:H, :W] = st
     tmax = pad.view(gy, th, gx, tw).amax(dim=(1, 3))
-    return {"buckets": int(((tmax + 31) // 32).sum()), "live_pixel_buckets": int(((st + 31) // 32).sum()),
-            "pixels": int(H * W)}
+    return {"bucket_entries": 64, "buckets": int(((tmax + 63) // 64).sum()),
+            "live_pixel_buckets": int(((st + 63) // 64).sum()), "pixels": int(H * W)}
 
 
 def bench_ours(args, rank, local_rank, world):

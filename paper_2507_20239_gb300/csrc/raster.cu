@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(kSplatThreads, kSplatBlocks) raster_bwd_splat_
         __syncwarp();
       }
       const int s1 = min(s0 + 32, nl + 31);
-#pragma unroll 4
+#pragma unroll 8
       for (int s = s0; s < s1; ++s) {
         const float4 *q = rw + ((s - lane) & (kSplatRing - 1));
         const float Tin = __shfl_up_sync(0xffffffffu, T, 1);
