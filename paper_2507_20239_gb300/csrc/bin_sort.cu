@@ -82,17 +82,19 @@ __device__ __forceinline__ uint64_t rs_count(const RsSrc &s, bool from_records) 
 
 // Visible-record count and the range of their FP32 depth bits (atomics on zeroed
 // words: range[0] collects the largest ~bits, i.e. the smallest bits).
-__global__ void __launch_bounds__(1024) depth_range_kernel(const int32_t *__restrict__ radius,
+__global__ void __launch_bounds__(256) depth_range_kernel(const int32_t *__restrict__ radius,
                                                           const float *__restrict__ depth, int64_t n,
                                                           uint32_t *n_vis, uint32_t *range) {
   uint32_t cnt = 0, mx = 0, nmn = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (radius[i] > 0) {
-      const uint32_t b = __float_as_uint(depth[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t rad = radius[i];
+    const uint32_t b = __float_as_uint(depth[i]);   // both loads in flight at once
+    if (rad > 0) {
       ++cnt;
       mx = max(mx, b);
       nmn = max(nmn, ~b);
     }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -146,8 +148,11 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(RsSrc src, uint3
   __syncthreads();
   if (FROM_RECORDS) {
     const uint32_t mn = ~src.range[0];
-    for (uint64_t i = begin + threadIdx.x; i < end; i += kRsThreads)
-      if (src.radius[i] > 0) atomicAdd(&h[warp][((__float_as_uint(src.depth[i]) - mn) >> shift) & mask], 1u);
+    for (uint64_t i = begin + threadIdx.x; i < end; i += kRsThreads) {
+      const int32_t rad = src.radius[i];
+      const uint32_t b = __float_as_uint(src.depth[i]);
+      if (rad > 0) atomicAdd(&h[warp][((b - mn) >> shift) & mask], 1u);
+    }
   } else {
     const uint32_t *keys = src.keys;
     uint64_t i = begin + 4 * threadIdx.x;
@@ -260,8 +265,10 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(RsSrc src, 
       const uint32_t li = warp * (32 * kRsItems) + j * 32 + lane;   // warp slice of 32 * kRsItems keys
       bool valid = li < tile_n;
       if (FROM_RECORDS) {
-        valid = valid && src.radius[tb + li] > 0;
-        k[j] = valid ? __float_as_uint(src.depth[tb + li]) - mn : 0u;
+        const int32_t rad = valid ? src.radius[tb + li] : 0;
+        const uint32_t b = valid ? __float_as_uint(src.depth[tb + li]) : 0u;
+        valid = rad > 0;
+        k[j] = valid ? b - mn : 0u;
         v[j] = (uint32_t)(tb + li);
       } else {
         k[j] = valid ? src.keys[tb + li] : 0u;
@@ -789,7 +796,7 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
 static gs_status_t depth_sort(const gs_proj_t *proj, int64_t R, const BinWs &w, uint32_t *n_vis,
                               uint32_t *range, cudaStream_t s) {
   const int G = radix_blocks();
-  depth_range_kernel<<<num_sms() * 2, 1024, 0, s>>>(proj->radius, proj->depth, R, n_vis, range);
+  depth_range_kernel<<<num_sms() * 4, 256, 0, s>>>(proj->radius, proj->depth, R, n_vis, range);
   GS_LAUNCH_CHECK();
   static const int kPass[4][2] = {{0, 8}, {8, 8}, {16, 8}, {24, 8}};   // (shift, bits)
   uint32_t *totals = w.hist + (size_t)kDepthBins * kMaxBlocks;
