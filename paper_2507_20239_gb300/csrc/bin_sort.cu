@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_scan_kernel(RsSrc src, uint32_t
 // records, the ragged end) take the sentinel digit BINS and are staged last.
 // keys_out null: the pass writes no keys. A depth-sort pass that ends the sort
 // writes only the record ids, to vals_last.
-template <int BINS, int SRC>
+template <int BINS, int SRC, int NBC>
 __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(RsSrc src, uint32_t *__restrict__ keys_out,
                                                                      uint32_t *__restrict__ vals_out,
                                                                      uint32_t *__restrict__ vals_last,
@@ -276,20 +276,33 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(RsSrc src, 
       }
       dig[j] = valid ? ((k[j] >> shift) & mask) : (uint32_t)BINS;
     }
-    // peers: the lanes holding the same digit, from one ballot per digit bit (and
-    // one for the sentinel bit)
+    // peers: the lanes holding the same digit, from one ballot per digit bit (a
+    // lane with bit value v keeps ballot ^ (v - 1): the ballot, or its complement),
+    // unrolled when the digit width is known at compile time; the sentinel bit takes
+    // one more, needed only where sentinels can occur (the ragged end of the keys,
+    // and the invisible records of the depth sort's first pass)
+    const bool sentinels = FROM_RECORDS || tile_n < (uint32_t)kRsTile;
     uint32_t pm[kRsItems];
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
       uint32_t p = 0xffffffffu;
-      for (int b = 0; b < src.nb; ++b) {
-        const bool bit = (dig[j] >> b) & 1u;
-        const uint32_t bb = __ballot_sync(0xffffffffu, bit);
-        p &= bit ? bb : ~bb;
+      if (NBC > 0) {
+#pragma unroll
+        for (int b = 0; b < NBC; ++b) {
+          const uint32_t bit = (dig[j] >> b) & 1u;
+          p &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+        }
+      } else {
+        for (int b = 0; b < src.nb; ++b) {
+          const uint32_t bit = (dig[j] >> b) & 1u;
+          p &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+        }
       }
-      const bool sb = dig[j] == (uint32_t)BINS;
-      const uint32_t bs = __ballot_sync(0xffffffffu, sb);
-      pm[j] = p & (sb ? bs : ~bs);
+      if (sentinels) {
+        const uint32_t sb = dig[j] == (uint32_t)BINS ? 1u : 0u;
+        p &= __ballot_sync(0xffffffffu, sb) ^ (sb - 1u);
+      }
+      pm[j] = p;
     }
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
@@ -779,8 +792,11 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     rs_scan_kernel<<<kRsBins, kRsThreads, 0, s>>>(src, hist, G, totals);
     GS_LAUNCH_CHECK();
     const bool last = p == passes - 1;
-    rs_downsweep_kernel<kRsBins, kSrcKeys><<<G, kRsThreads, 0, s>>>(src, (last && !keep_keys) ? nullptr : ko, vo,
-                                                                    nullptr, hist, totals);
+    uint32_t *kw = (last && !keep_keys) ? nullptr : ko;
+    if (nb == 8)
+      rs_downsweep_kernel<kRsBins, kSrcKeys, 8><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
+    else
+      rs_downsweep_kernel<kRsBins, kSrcKeys, 0><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
     GS_LAUNCH_CHECK();
     cur0 = !cur0;
   }
@@ -815,9 +831,9 @@ static gs_status_t depth_sort(const gs_proj_t *proj, int64_t R, const BinWs &w, 
     rs_scan_kernel<<<kDepthBins, kRsThreads, 0, s>>>(src, w.hist, G, totals);
     GS_LAUNCH_CHECK();
     if (p == 0) {
-      rs_downsweep_kernel<kDepthBins, kSrcRecords><<<G, kRsThreads, 0, s>>>(src, ko, vo, w.order, w.hist, totals);
+      rs_downsweep_kernel<kDepthBins, kSrcRecords, 8><<<G, kRsThreads, 0, s>>>(src, ko, vo, w.order, w.hist, totals);
     } else {
-      rs_downsweep_kernel<kDepthBins, kSrcDepthKeys><<<G, kRsThreads, 0, s>>>(src, ko, vo, w.order, w.hist,
+      rs_downsweep_kernel<kDepthBins, kSrcDepthKeys, 8><<<G, kRsThreads, 0, s>>>(src, ko, vo, w.order, w.hist,
                                                                               totals);
     }
     GS_LAUNCH_CHECK();
