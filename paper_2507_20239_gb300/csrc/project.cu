@@ -151,23 +151,29 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
     const int v = (int)(r / P.n);
     const int64_t g = r - (int64_t)v * P.n;
     const gs_camera_t &cam = cams[v];
+    // every geometric input is requested at once (the few records behind the near
+    // plane read 32 bytes they do not use), so a record waits for one round trip
+    // before its SH row instead of two
     const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
+    const float4 q = reinterpret_cast<const float4 *>(P.quats)[g];
+    const float ls0 = P.log_scales[3 * g + 0], ls1 = P.log_scales[3 * g + 1], ls2 = P.log_scales[3 * g + 2];
+    const float logit = P.opacity_logits[g];
     ProjGeom G;
     camera_space(cam, mx, my, mz, G.tx, G.ty, G.tz);
     bool ok = G.tz > cam.near_plane;
     int radius = 0, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     float u = 0.f, vv = 0.f, A = 0.f, B = 0.f, C = 0.f, qmax = 0.f;   // (A, B, C) = (A, beta, gamma)
+    float o_ = 0.f;
     if (ok) {
-      const float4 q = reinterpret_cast<const float4 *>(P.quats)[g];
       const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
       const Rot Rq = quat_rot(q.x * inv, q.y * inv, q.z * inv, q.w * inv);
-      const float s0 = expf(P.log_scales[3 * g + 0]);
-      const float s1 = expf(P.log_scales[3 * g + 1]);
-      const float s2 = expf(P.log_scales[3 * g + 2]);
+      const float s0 = expf(ls0);
+      const float s1 = expf(ls1);
+      const float s2 = expf(ls2);
       float M[9];
       scale_rot(Rq, s0, s1, s2, M);
       project_cov(cam, M, G);
-      const float o_ = 1.f / (1.f + expf(-P.opacity_logits[g]));
+      o_ = 1.f / (1.f + expf(-logit));
       ok = G.det > 0.f && o_ >= kAlphaMin;
       if (ok) {
         // factored conic: A = c/det, beta = -b/c, gamma = 1/c
@@ -235,9 +241,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
       });
     }
     const uint8_t cl = (cr < 0.f ? 1 : 0) | (cg < 0.f ? 2 : 0) | (cb < 0.f ? 4 : 0);
-    const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
     reinterpret_cast<float2 *>(out.mean2d)[r] = make_float2(u, vv);
-    reinterpret_cast<float4 *>(out.conic_opacity)[r] = make_float4(A, B, C, o);
+    reinterpret_cast<float4 *>(out.conic_opacity)[r] = make_float4(A, B, C, o_);
     reinterpret_cast<float4 *>(out.rgb)[r] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cb, 0.f), qmax);
     out.depth[r] = G.tz;
     out.radius[r] = radius;
@@ -250,6 +255,10 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(gs_params_t P, const g
 // Projection VJP, geometric part: conic, pixel mean and opacity gradients of every
 // view -> means (through t = W mu + t_w and J), log-scales, quaternion, opacity
 // logit; the densification statistic is fused. The colour part is project_bwd_sh.
+// Every input is requested at entry, before the visibility test (with several views
+// the per-view records follow it): the parameters of a Gaussian no view sees are read
+// and not used, but a thread waits for one round trip instead of two.
+template <bool ONE_VIEW>
 __global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(gs_params_t P, const gs_camera_t *__restrict__ cams,
                                                                int n_views, gs_proj_t proj, gs_rec_grads_t rg,
                                                                gs_param_grads_t out, float *accum, int32_t *count) {
@@ -257,6 +266,17 @@ __global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(gs_params_t P,
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     {
     const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
+    const float4 q = reinterpret_cast<const float4 *>(P.quats)[g];
+    const float ls0 = P.log_scales[3 * g + 0], ls1 = P.log_scales[3 * g + 1], ls2 = P.log_scales[3 * g + 2];
+    const float logit = P.opacity_logits[g];
+    int rad1 = 0;
+    float2 gm1 = make_float2(0.f, 0.f);
+    float4 gco1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ONE_VIEW) {
+      rad1 = proj.radius[g];
+      gm1 = reinterpret_cast<const float2 *>(rg.d_mean2d)[g];
+      gco1 = reinterpret_cast<const float4 *>(rg.d_conic_opacity)[g];
+    }
     float d_mean[3] = {0.f, 0.f, 0.f};
     float dM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // dL/dM, M = R S
     float d_logit = 0.f;
@@ -264,28 +284,26 @@ __global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(gs_params_t P,
     int cnt = count ? count[g] : 0;
     bool any = false;
     // view-independent pieces, computed on first use
-    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     float qinv = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f, M[9];
     Rot Rq;
-    for (int v = 0; v < n_views; ++v) {
+    for (int v = 0; v < (ONE_VIEW ? 1 : n_views); ++v) {
       const int64_t r = (int64_t)v * n + g;
-      if (proj.radius[r] <= 0) continue;
+      if ((ONE_VIEW ? rad1 : proj.radius[r]) <= 0) continue;
       const gs_camera_t &cam = cams[v];
       if (!any) {
         any = true;
-        q = reinterpret_cast<const float4 *>(P.quats)[g];
         qinv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
         Rq = quat_rot(q.x * qinv, q.y * qinv, q.z * qinv, q.w * qinv);
-        s0 = expf(P.log_scales[3 * g + 0]);
-        s1 = expf(P.log_scales[3 * g + 1]);
-        s2 = expf(P.log_scales[3 * g + 2]);
+        s0 = expf(ls0);
+        s1 = expf(ls1);
+        s2 = expf(ls2);
         scale_rot(Rq, s0, s1, s2, M);
       }
       ProjGeom G;
       camera_space(cam, mx, my, mz, G.tx, G.ty, G.tz);
       project_cov(cam, M, G);
-      const float2 gm = reinterpret_cast<const float2 *>(rg.d_mean2d)[r];
-      const float4 gco = reinterpret_cast<const float4 *>(rg.d_conic_opacity)[r];
+      const float2 gm = ONE_VIEW ? gm1 : reinterpret_cast<const float2 *>(rg.d_mean2d)[r];
+      const float4 gco = ONE_VIEW ? gco1 : reinterpret_cast<const float4 *>(rg.d_conic_opacity)[r];
       if (accum) {
         const float gx = __fmul_rn(gm.x, 0.5f * (float)cam.width);
         const float gy = __fmul_rn(gm.y, 0.5f * (float)cam.height);
@@ -344,7 +362,7 @@ __global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(gs_params_t P,
       d_mean[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
       d_mean[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
       // opacity = sigmoid(logit)
-      const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
+      const float o = 1.f / (1.f + expf(-logit));
       d_logit += gco.w * o * (1.f - o);
     }
     float d_ls[3] = {0.f, 0.f, 0.f};
@@ -419,11 +437,25 @@ __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
     const int64_t g = base + threadIdx.x;
     const int64_t g0 = base + wib * 32;
     const int rows = (int)(n - g0 < 0 ? 0 : (n - g0 > 32 ? 32 : n - g0));
+    // with one view, the record's inputs are requested before the row staging, so
+    // they arrive while it runs
+    int rad1 = 0;
+    float mx1 = 0.f, my1 = 0.f, mz1 = 0.f;
+    float4 grgb1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint8_t cl1 = 0;
+    if (ONE_VIEW && g < n) {
+      rad1 = proj.radius[g];
+      mx1 = P.means[3 * g + 0]; my1 = P.means[3 * g + 1]; mz1 = P.means[3 * g + 2];
+      grgb1 = reinterpret_cast<const float4 *>(rg.d_rgb)[g];
+      cl1 = proj.clamped[g];
+    }
     if (STAGED) {
       // rows of Gaussians culled in every view are not read: their coefficients are
       // never used and their gradient rows are zero
       bool seen = false;
-      if (g < n)
+      if (ONE_VIEW)
+        seen = rad1 > 0;
+      else if (g < n)
         for (int v = 0; v < n_views && !seen; ++v) seen = proj.radius[(int64_t)v * n + g] > 0;
       const uint32_t vmask = __ballot_sync(0xffffffffu, seen);
       const float *src = P.sh + g0 * RW;
@@ -447,16 +479,17 @@ __global__ void __launch_bounds__(128, ONE_VIEW ? 8 : 4) project_bwd_sh_kernel(
 #pragma unroll
         for (int k = 0; k < RW; ++k) dsh_row[k] = 0.f;
       }
-      const float mx = P.means[3 * g + 0], my = P.means[3 * g + 1], mz = P.means[3 * g + 2];
+      const float mx = ONE_VIEW ? mx1 : P.means[3 * g + 0], my = ONE_VIEW ? my1 : P.means[3 * g + 1],
+                  mz = ONE_VIEW ? mz1 : P.means[3 * g + 2];
       float dm0 = 0.f, dm1 = 0.f, dm2 = 0.f;
       bool any = false;
-      for (int v = 0; v < n_views; ++v) {
+      for (int v = 0; v < (ONE_VIEW ? 1 : n_views); ++v) {
         const int64_t r = (int64_t)v * n + g;
-        if (proj.radius[r] <= 0) continue;
+        if ((ONE_VIEW ? rad1 : proj.radius[r]) <= 0) continue;
         any = true;
         const gs_camera_t &cam = cams[v];
-        const float4 grgb = reinterpret_cast<const float4 *>(rg.d_rgb)[r];
-        const uint8_t cl = proj.clamped[r];
+        const float4 grgb = ONE_VIEW ? grgb1 : reinterpret_cast<const float4 *>(rg.d_rgb)[r];
+        const uint8_t cl = ONE_VIEW ? cl1 : proj.clamped[r];
         const float g0c = (cl & 1) ? 0.f : grgb.x, g1c = (cl & 2) ? 0.f : grgb.y, g2c = (cl & 4) ? 0.f : grgb.z;
         float ccx, ccy, ccz;
         camera_centre(cam, ccx, ccy, ccz);
@@ -540,7 +573,10 @@ __global__ void densify_accum_kernel(const float *__restrict__ d_mean2d, const i
 template <int DEG, bool STAGED>
 static void launch_bwd_k(int grid, cudaStream_t s, const gs_params_t &P, const gs_frame_t *frame, const gs_proj_t &proj,
                          const gs_rec_grads_t &rg, const gs_param_grads_t &out, float *acc, int32_t *cnt) {
-  project_bwd_geom_kernel<<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
+  if (frame->n_views == 1)
+    project_bwd_geom_kernel<true><<<grid, 128, 0, s>>>(P, frame->cams_dev, 1, proj, rg, out, acc, cnt);
+  else
+    project_bwd_geom_kernel<false><<<grid, 128, 0, s>>>(P, frame->cams_dev, frame->n_views, proj, rg, out, acc, cnt);
   count_launch();
   // float4 staging needs both SH arrays on 16-byte boundaries (rows of 3K floats, K = 4 or 16)
   const bool vec = (reinterpret_cast<uintptr_t>(P.sh) & 15u) == 0 && (reinterpret_cast<uintptr_t>(out.d_sh) & 15u) == 0;
