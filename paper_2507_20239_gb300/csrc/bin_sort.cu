@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(256) depth_range_kernel(const int32_t *__restr
 // Digit histograms per block (digit-major: hist[d * G + b]).
 // Element sources of a pass: plain keys, depth-sort keys (the pass may be inactive
 // or end the sort), or the records themselves (the depth sort's first pass).
-constexpr int kSrcKeys = 0, kSrcDepthKeys = 1, kSrcRecords = 2;
+// kSrcPacked: (key, value) pairs stored as one uint2 each (the emission's output when a
+// single tile-id pass follows).
+constexpr int kSrcKeys = 0, kSrcDepthKeys = 1, kSrcRecords = 2, kSrcPacked = 3;
 
 template <int BINS, int SRC>
 __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(RsSrc src, uint32_t *hist) {
@@ -153,6 +155,16 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_kernel(RsSrc src, uint3
       const uint32_t b = __float_as_uint(src.depth[i]);
       if (rad > 0) atomicAdd(&h[warp][((b - mn) >> shift) & mask], 1u);
     }
+  } else if (SRC == kSrcPacked) {
+    // two pairs per 16-byte load (chunks start at even indices)
+    const uint2 *pk = reinterpret_cast<const uint2 *>(src.keys);
+    uint64_t i = begin + 2 * threadIdx.x;
+    for (; i + 1 < end; i += 2 * kRsThreads) {
+      const uint4 k = *reinterpret_cast<const uint4 *>(pk + i);
+      atomicAdd(&h[warp][(k.x >> shift) & mask], 1u);
+      atomicAdd(&h[warp][(k.z >> shift) & mask], 1u);
+    }
+    for (; i < end; ++i) atomicAdd(&h[warp][(pk[i].x >> shift) & mask], 1u);
   } else {
     const uint32_t *keys = src.keys;
     uint64_t i = begin + 4 * threadIdx.x;
@@ -230,7 +242,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(RsSrc src, 
   uint64_t begin, end;
   chunk_of(n, G, kRsTile, begin, end);
   if (begin >= end) return;
-  const bool last = SRC != kSrcKeys && depth_key_bits(src.range) <= src.shift + src.nb;
+  const bool last = (SRC == kSrcRecords || SRC == kSrcDepthKeys) && depth_key_bits(src.range) <= src.shift + src.nb;
   uint32_t *ko = last ? nullptr : keys_out;
   uint32_t *vo = last ? vals_last : vals_out;
   const int shift = src.shift;
@@ -270,6 +282,10 @@ __global__ void __launch_bounds__(kRsThreads, 4) rs_downsweep_kernel(RsSrc src, 
         valid = rad > 0;
         k[j] = valid ? b - mn : 0u;
         v[j] = (uint32_t)(tb + li);
+      } else if (SRC == kSrcPacked) {
+        const uint2 kv = valid ? reinterpret_cast<const uint2 *>(src.keys)[tb + li] : make_uint2(0u, 0u);
+        k[j] = kv.x;
+        v[j] = kv.y;
       } else {
         k[j] = valid ? src.keys[tb + li] : 0u;
         v[j] = valid ? src.vals[tb + li] : 0u;
@@ -548,6 +564,10 @@ __global__ void __launch_bounds__(256) bin_count_kernel(gs_proj_t P, const uint3
   }
 }
 
+// PACKED: each hit is written as one 8-byte (tile, record) pair at dkeys (as uint2)
+// instead of two 4-byte words in two arrays: the scattered stores are what the
+// emission's time goes to, and one store per hit halves their sectors.
+template <bool PACKED>
 __global__ void __launch_bounds__(256) bin_emit_kernel(const uint32_t *__restrict__ order, const uint32_t *n_vis,
                                                        const uint32_t *overflow, int fbits,
                                                        const uint32_t *__restrict__ hist,
@@ -660,8 +680,12 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const uint32_t *__restric
         if (hit) {
           const uint32_t pos = cur + __popc(peers & lt);
           if (GS_CHECK(pos < cap, 4, pos)) {
-            dkeys[pos] = tile;
-            dvals[pos] = r;
+            if (PACKED) {
+              reinterpret_cast<uint2 *>(dkeys)[pos] = make_uint2(tile, r);
+            } else {
+              dkeys[pos] = tile;
+              dvals[pos] = r;
+            }
           }
           if ((peers & lt) == 0) s_cur[wib][dig] = cur + __popc(peers);
         }
@@ -754,6 +778,7 @@ static BinWs bin_ws_layout(void *base, int64_t R, int64_t cap, int fbits) {
   w.dhist = (uint32_t *)take(4 * ((((size_t)R + 31) / 32) << fbits) + 16);
   w.ubatch = (uint2 *)take(8 * (((size_t)R + 31) / 32) + 16);
   w.dk0 = (uint32_t *)take(4 * (size_t)cap + 16);
+  // dk1 and dv1 are adjacent: together they hold cap packed 8-byte (tile, record) pairs
   w.dk1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.dv1 = (uint32_t *)take(4 * (size_t)cap + 16);
   w.block_sums = (uint64_t *)take(8 * kMaxBlocks);
@@ -773,9 +798,10 @@ static int radix_blocks() {
 
 // Stable LSD radix sort of (key, val) pairs on bits [first_bit, n_bits), ping-ponging between
 // buffer 0 and 1; returns in *in_b0 whether the result is in buffer 0.
+// packed: the first pass reads buffer 0 as (key, value) uint2 pairs at k0.
 static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const uint32_t *d_n,
                               const uint32_t *d_skip, int first_bit, int n_bits, bool keep_keys, uint32_t *hist,
-                              cudaStream_t s, bool *in_b0) {
+                              cudaStream_t s, bool *in_b0, bool packed = false) {
   const int G = radix_blocks();
   const int span = n_bits - first_bit;
   const int passes = span > 0 ? (span + 7) / 8 : 0;
@@ -787,13 +813,21 @@ static gs_status_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
     const int nb = (shift + bits > n_bits) ? n_bits - shift : bits;
     uint32_t *ki = cur0 ? k0 : k1, *vi = cur0 ? v0 : v1, *ko = cur0 ? k1 : k0, *vo = cur0 ? v1 : v0;
     const RsSrc src{ki, vi, nullptr, nullptr, 0, d_n, d_skip, nullptr, shift, nb};
-    rs_upsweep_kernel<kRsBins, kSrcKeys><<<G, kRsThreads, 0, s>>>(src, hist);
+    const bool pk = packed && p == 0;
+    if (pk)
+      rs_upsweep_kernel<kRsBins, kSrcPacked><<<G, kRsThreads, 0, s>>>(src, hist);
+    else
+      rs_upsweep_kernel<kRsBins, kSrcKeys><<<G, kRsThreads, 0, s>>>(src, hist);
     GS_LAUNCH_CHECK();
     rs_scan_kernel<<<kRsBins, kRsThreads, 0, s>>>(src, hist, G, totals);
     GS_LAUNCH_CHECK();
     const bool last = p == passes - 1;
     uint32_t *kw = (last && !keep_keys) ? nullptr : ko;
-    if (nb == 8)
+    if (pk && nb == 8)
+      rs_downsweep_kernel<kRsBins, kSrcPacked, 8><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
+    else if (pk)
+      rs_downsweep_kernel<kRsBins, kSrcPacked, 0><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
+    else if (nb == 8)
       rs_downsweep_kernel<kRsBins, kSrcKeys, 8><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
     else
       rs_downsweep_kernel<kRsBins, kSrcKeys, 0><<<G, kRsThreads, 0, s>>>(src, kw, vo, nullptr, hist, totals);
@@ -925,9 +959,17 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   if (gs_status_t st = run_scan(hs, w.block_sums, G, s)) return st;
   // 4. emit (tile, record) partitioned by the low digit, in depth order within it,
   //    into the buffer the remaining passes end in
-  bin_emit_kernel<<<eg, 256, 0, s>>>(order, n_vis, overflow, fbits, w.dhist, w.ubatch, ut0, uinf,
-                                     emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v, w.counters + 4,
-                                     (uint64_t)bins->capacity);
+  //    With exactly one pass to follow (9-16 tile-id bits), the hits go out as packed
+  //    (tile, record) pairs over the contiguous workspace words dk1 | dv1, which
+  //    hold 8 * capacity bytes, and that pass reads them.
+  const bool packed = passes == 1;
+  if (packed)
+    bin_emit_kernel<true><<<eg, 256, 0, s>>>(order, n_vis, overflow, fbits, w.dhist, w.ubatch, ut0, uinf, B_k,
+                                             nullptr, w.counters + 4, (uint64_t)bins->capacity);
+  else
+    bin_emit_kernel<false><<<eg, 256, 0, s>>>(order, n_vis, overflow, fbits, w.dhist, w.ubatch, ut0, uinf,
+                                              emit_to_A ? A_k : B_k, emit_to_A ? A_v : B_v, w.counters + 4,
+                                              (uint64_t)bins->capacity);
   GS_LAUNCH_CHECK();
   // 5. stable sort by the remaining tile-id bits
   bool res0 = true;
@@ -935,7 +977,8 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
     if (gs_status_t st = radix_sort(A_k, A_v, B_k, B_v, m_total, overflow, fbits, tile_bits, true, w.hist, s, &res0))
       return st;
   } else {
-    if (gs_status_t st = radix_sort(B_k, B_v, A_k, A_v, m_total, overflow, fbits, tile_bits, true, w.hist, s, &res0))
+    if (gs_status_t st = radix_sort(B_k, B_v, A_k, A_v, m_total, overflow, fbits, tile_bits, true, w.hist, s, &res0,
+                                    packed))
       return st;
     res0 = !res0;
   }
