@@ -94,11 +94,16 @@ typedef struct {
 } gs_params_t;
 
 /* Projected records (device, caller-allocated, n_records = n_views * n rows each).
- * mean2d [R][2] pixels; conic_opacity [R][4] = (A, B, C, opacity) with the Gaussian
- * power P = -1/2 (A dx^2 + C dy^2) - B dx dy, (A B; B C) = (Sigma' + 0.3 I)^-1;
- * rgb [R][4] = (r, g, b, 0); depth [R] camera-space z; radius [R] = ceil(3 sqrt(
- * lambda_max)), 0 = culled; rect [R][4] tile rectangle x0, y0, x1, y1 (exclusive);
- * clamped [R] bit c set when colour channel c was clamped at 0. */
+ * mean2d [R][2] pixels; conic_opacity [R][4] = (A, beta, gamma, opacity): with the
+ * dilated covariance Sigma'' = Sigma' + 0.3 I = (a b; b c), det = ac - b^2,
+ * A = c/det, beta = -b/c, gamma = 1/c, so that d^T Sigma''^-1 d = A (dx + beta dy)^2
+ * + gamma dy^2 (d = pixel mean - pixel centre) and the falloff is exp(-1/2 of it);
+ * rgb [R][4] = (r, g, b, q_max), q_max = 2 ln(255 opacity), the bound on
+ * d^T Sigma''^-1 d where alpha can reach 1/255; depth [R] camera-space z;
+ * radius [R] = the ceiling of the larger half-extent of that ellipse (with the
+ * binning's 0.2% margin), 0 = culled; rect [R][4] tile rectangle x0, y0, x1, y1
+ * (exclusive) under its bounding box; clamped [R] bit c set when colour channel c
+ * was clamped at 0. */
 typedef struct {
   float *mean2d;
   float *conic_opacity;
@@ -182,9 +187,11 @@ size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t dup_capacity, const
 /* EWA projection + SH colour of every (view, Gaussian) record -- Eq. 1, the paper's
  * Sigma' = J W Sigma W^T J^T, and the SH-evaluated colour c_i of Eq. 2.
  * Readings: near-plane cull; J at the mean with t_x/t_z, t_y/t_z clamped to
- * +-1.3 (W/2)/f; Sigma' + 0.3 I; cull det <= 0; radius = ceil(3 sqrt(m +
- * sqrt(max(0.1, m^2 - det)))); cull when the tile rectangle is empty.
- * Culled records get radius 0 and an empty rect; their other fields are zero. */
+ * +-1.3 (W/2)/f; Sigma' + 0.3 I; cull det <= 0 and opacity < 1/255; the footprint
+ * is the ellipse where alpha = min(0.99, opacity G) can reach 1/255, d^T Sigma''^-1 d
+ * <= 2 ln(255 opacity) (x 1.002), and radius and rect come from its half-extents;
+ * cull when the tile rectangle is empty. Culled records get radius 0 and an empty
+ * rect; their other fields are zero. */
 gs_status_t gs_project(const gs_params_t *params, const gs_frame_t *frame, gs_proj_t *out,
                        gs_stream_t stream);
 
