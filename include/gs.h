@@ -247,8 +247,9 @@ gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs
  * lineage that the paper's base trainer uses; a measured alternative to
  * gs_raster_bwd, chosen by the autotuner). Same gradient as gs_raster_bwd (up to
  * summation order), parallel over list entries: each tile's list is cut into
- * buckets of 32 entries, one lane per entry, and the tile's pixels flow through
- * each bucket from a checkpoint the forward stored at its first position.
+ * buckets of 64 entries, two consecutive entries per lane, and the tile's pixels
+ * flow through each bucket from a checkpoint the forward stored at its first
+ * position.
  *
  * Checkpoints are stored per (bucket, 8 x 8 pixel block) that the forward actually
  * walks, in 1 KB slots (64 pixels x float4); a table of 4 bytes per possible
@@ -262,11 +263,12 @@ gs_status_t gs_raster_bwd(const gs_proj_t *proj, const gs_bins_t *bins, const gs
  *
  * gs_raster_ckpt_size: bytes of a checkpoint buffer with n_slots slots for a frame
  * whose lists hold at most `capacity` entries (the gs_bins_t capacity); n_slots < 0
- * gives a slot for every (bucket, block) pair, (ceil(capacity / 32) + n_tiles) x
- * tile_w tile_h / 64. 0 for an invalid frame or capacity.
+ * gives a slot for every possible (32-entry table row, block) pair, (ceil(capacity
+ * / 32) + n_tiles) x tile_w tile_h / 64 (only every other row is used). 0 for an
+ * invalid frame or capacity.
  *
  * gs_raster_fwd_ckpt: gs_raster_fwd that always writes stop [n_pixels] and also,
- * for every pixel still compositing at list position 32 b of its tile, the float4
+ * for every pixel still compositing at list position 64 b of its tile, the float4
  * (T, R, G, B) of the state before that position (transmittance and the colour
  * composited so far) into ckpt. ckpt: device, 16-byte aligned, ckpt_bytes at least
  * gs_raster_ckpt_size(frame, bins->capacity, 0); its slot count is what the bytes
