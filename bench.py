@@ -275,38 +275,51 @@ def bench_ours(args, rank, local_rank, world):
                           "splat_buckets": splat_bucket_stats(step)}), flush=True)
         return None
     # ---- end to end: camera + target H2D from pinned memory, loss D2H, every step
+    # Two input buffers (camera block and target image), each with the step captured
+    # over it: while one graph runs, the next step's camera and target are copied from
+    # pinned host memory straight into the other buffer on a side stream (as a
+    # training loop prefetches its next view), so the compute stream carries no
+    # device-to-device move. Every one of the K host-to-device copies is issued after
+    # e0 and waited for before e1; each step's loss is copied back to pinned memory.
     tgt_host = step.target.cpu().pin_memory()
     cam_host = step.frame.cams_dev.cpu().pin_memory()
     loss_host = torch.empty(frame.n_views, pin_memory=True)
+    cams_a, tgt_a, ptr_a = step.frame.cams_dev, step.target, step.frame.frame.cams_dev
+    cams_b, tgt_b = cams_a.clone(), tgt_a.clone()
+    step.frame.frame.cams_dev, step.target = cams_b.data_ptr(), tgt_b
+    graph_b = step.capture()
+    step.frame.frame.cams_dev, step.target = ptr_a, tgt_a
+    bufs = [(cams_a, tgt_a, graph), (cams_b, tgt_b, graph_b)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(2):
-        step.target.copy_(tgt_host, non_blocking=True)
-        graph.replay()
+    for cams_i, tgt_i, g_i in bufs:
+        cams_i.copy_(cam_host, non_blocking=True)
+        tgt_i.copy_(tgt_host, non_blocking=True)
+        g_i.replay()
     torch.cuda.synchronize()
-    # the next step's target is copied from pinned host memory on a side stream while
-    # the current step runs (as a training loop prefetches its next view), then moved
-    # into the step's buffer on the compute stream; every one of the K host-to-device
-    # copies is issued after e0 and waited for before e1
     cur = torch.cuda.current_stream()
     side = torch.cuda.Stream(device=dev)
-    staging = torch.empty_like(step.target)
-    ready = torch.cuda.Event()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def prefetch(i):
+        with torch.cuda.stream(side):
+            bufs[i][0].copy_(cam_host, non_blocking=True)
+            bufs[i][1].copy_(tgt_host, non_blocking=True)
+            ready[i].record(side)
+
     e0.record()
     side.wait_stream(cur)
-    with torch.cuda.stream(side):
-        staging.copy_(tgt_host, non_blocking=True)
-        ready.record(side)
+    prefetch(0)
     for k in range(args.steps):
-        cur.wait_event(ready)
-        step.frame.cams_dev.copy_(cam_host, non_blocking=True)
-        step.target.copy_(staging, non_blocking=True)
+        i = k % 2
         if k + 1 < args.steps:
-            side.wait_stream(cur)            # staging is free once the move above is done
-            with torch.cuda.stream(side):
-                staging.copy_(tgt_host, non_blocking=True)
-                ready.record(side)
-        graph.replay()
+            if k >= 1:
+                side.wait_event(done[1 - i])   # the step that last read that buffer
+            prefetch(1 - i)
+        cur.wait_event(ready[i])
+        bufs[i][2].replay()
+        done[i].record(cur)
         loss_host.copy_(step.loss, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
@@ -384,8 +397,8 @@ def bench_ours(args, rank, local_rank, world):
         "gpu_launches_per_step": int(launches),
         "timing": {"value": "CUDA-graph replay of the step, events around the K replays",
                    "e2e": "every step: camera and target image from pinned host memory (the next "
-                          "step's target copied on a side stream while the current step runs), "
-                          "loss read back",
+                          "step's copied on a side stream into the second of two input buffers, each "
+                          "with its own captured graph, while the current step runs), loss read back",
                    "stages": "the same step launched eagerly for K steps just before, events between stages",
                    "eager_ms_per_step": round(eager_ms, 4)},
         "roofline": roof,
