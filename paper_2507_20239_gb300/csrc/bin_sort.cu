@@ -18,9 +18,10 @@
 //      digit of that sort (the low FB bits of the tile id) is fused into the
 //      emission: a counting pass histograms each warp batch's hits by that digit,
 //      a scan turns the (digit, batch) counts into cursors, and the emitting pass
-//      writes every entry straight to its digit-partitioned position. The remaining
-//      high bits take ceil((bits - FB) / 8) ordinary passes (none when the tile id
-//      has at most 8 bits).
+//      writes every entry straight to its digit-partitioned position (as one packed
+//      8-byte (tile, record) pair when a single pass follows). The remaining high
+//      bits take ceil((bits - FB) / 8) ordinary passes (none when the tile id has at
+//      most 8 bits).
 // A stable sort by tile of a depth-ordered sequence is ordered by (tile, depth,
 // record). Stage 2 moves 8 bytes per duplicate per pass instead of 12 bytes per
 // pass for 5-6 passes.
