@@ -231,6 +231,59 @@ __device__ __forceinline__ void warp_copy_rows(const T *__restrict__ src, T *__r
   }
 }
 
+// The same copy in 16-byte vectors, for rows of w = 4 w4 floats whose arrays start on
+// 16-byte boundaries (quaternions, SH rows, their optimiser moments: most of the
+// bytes): four times the bytes in flight per load, which is what this latency-bound
+// copy is short of.
+__device__ __forceinline__ void warp_copy_rows4(const float4 *__restrict__ src, float4 *__restrict__ dst, int w4,
+                                                int64_t g0, int cnt, const int64_t *ds, const int64_t *dc,
+                                                const int64_t *dp, bool children, bool zero_new, int lane) {
+  const int tot = cnt * w4;
+  const int q = 32 / w4, rem = 32 - q * w4;
+  int r = lane / w4, c = lane - (lane / w4) * w4;
+  const float4 *s = src + g0 * w4;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  constexpr int U = 4;
+  for (int e0 = lane; e0 < tot; e0 += 32 * U) {
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = e0 + 32 * u < tot ? s[e0 + 32 * u] : z;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e0 + 32 * u < tot) {
+        const float4 nv = zero_new ? z : v[u];
+        const int64_t a = ds[r], b = dc[r];
+        if (a >= 0) dst[a * w4 + c] = v[u];
+        if (b >= 0) dst[b * w4 + c] = nv;
+        if (children) {
+          const int64_t d = dp[r];
+          if (d >= 0) {
+            dst[d * w4 + c] = nv;
+            dst[(d + 1) * w4 + c] = nv;
+          }
+        }
+      }
+      r += q;
+      c += rem;
+      if (c >= w4) {
+        c -= w4;
+        ++r;
+      }
+    }
+  }
+}
+
+// Row copy of a float array: in 16-byte vectors where the width and alignment allow.
+__device__ __forceinline__ void copy_rows(const float *src, float *dst, int w, int64_t g0, int cnt,
+                                          const int64_t *ds, const int64_t *dc, const int64_t *dp, bool children,
+                                          bool zero_new, int lane) {
+  if ((w & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0)
+    warp_copy_rows4(reinterpret_cast<const float4 *>(src), reinterpret_cast<float4 *>(dst), w >> 2, g0, cnt, ds, dc,
+                    dp, children, zero_new, lane);
+  else
+    warp_copy_rows(src, dst, w, g0, cnt, ds, dc, dp, children, zero_new, lane);
+}
+
 constexpr int kScatThreads = 256;
 
 // Compaction, one warp per batch of 32 consecutive Gaussians: each lane finds its
@@ -273,11 +326,11 @@ __global__ void __launch_bounds__(kScatThreads) scatter_kernel(
     __syncwarp();
     warp_copy_rows(in.means, out.means, 3, g0, cnt, ds, dc, dp, false, false, lane);
     warp_copy_rows(in.log_scales, out.log_scales, 3, g0, cnt, ds, dc, dp, false, false, lane);
-    warp_copy_rows(in.quats, out.quats, 4, g0, cnt, ds, dc, dp, true, false, lane);
+    copy_rows(in.quats, out.quats, 4, g0, cnt, ds, dc, dp, true, false, lane);
     warp_copy_rows(in.opacity_logits, out.opacity_logits, 1, g0, cnt, ds, dc, dp, true, false, lane);
-    warp_copy_rows(in.sh, out.sh, shw, g0, cnt, ds, dc, dp, true, false, lane);
+    copy_rows(in.sh, out.sh, shw, g0, cnt, ds, dc, dp, true, false, lane);
     for (int e = 0; e < extra.n; ++e)
-      warp_copy_rows(extra.a[e].src, extra.a[e].dst, extra.a[e].width, g0, cnt, ds, dc, dp, true, true, lane);
+      copy_rows(extra.a[e].src, extra.a[e].dst, extra.a[e].width, g0, cnt, ds, dc, dp, true, true, lane);
     if (prov.origin_in != nullptr && g < in.n && keep) {
       const int32_t po = prov.origin_in[g], ps = prov.splits_in[g], pc = prov.clones_in[g];
       if (ds[lane] >= 0) {
@@ -445,7 +498,17 @@ extern "C" gs_status_t gs_densify_apply(const gs_densify_cfg_t *cfg, const gs_pa
     if (gs_status_t st = run_scan(f, w.block_sums, G, s)) return st;
   }
   int sg = (int)((in->n + 32 * (kScatThreads / 32) - 1) / (32 * (kScatThreads / 32)));
-  if (sg > num_sms() * 8) sg = num_sms() * 8;
+  // at most the blocks the device keeps resident: with more, a second partial wave
+  // of the grid-stride loop runs on a part of the GPU
+  static int resident = 0;
+  if (resident == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scatter_kernel, kScatThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 4;
+    resident = per_sm * num_sms();
+  }
+  if (sg > resident) sg = resident;
   scatter_kernel<<<sg, kScatThreads, 0, s>>>(*cfg, *in, split, clone, d_tau_logit, *out, el, pv, w.pos_s,
                                                       w.pos_c, w.pos_p, w.totals, out_capacity, d_new_n, d_error);
   GS_LAUNCH_CHECK();
