@@ -210,20 +210,49 @@ __global__ void adam_kernel(gs_params_out_t P, gs_param_grads_t G, gs_adam_state
   }
   float *m = S.m[grp], *v = S.v[grp];
   const float ss = step_size.v[grp];
-  const int64_t total = n * width;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    if (radius) {
-      const int64_t row = i / width;
-      bool seen = false;
-      for (int k = 0; k < n_views; ++k) seen |= radius[(int64_t)k * n + row] > 0;
-      if (!seen) continue;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto visible = [&](int64_t row) {
+    bool seen = false;
+    for (int k = 0; k < n_views; ++k) seen |= radius[(int64_t)k * n + row] > 0;
+    return seen;
+  };
+  auto update = [&](float &pi, float &mi, float &vi, float gi) {
+    mi = beta1 * mi + (1.f - beta1) * gi;
+    vi = beta2 * vi + (1.f - beta2) * gi * gi;
+    pi -= ss * mi / (sqrtf(vi) / sqrt_bc2 + eps);
+  };
+  const bool vec = (width & 3) == 0 && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                                         reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15u) == 0;
+  if (vec) {
+    // rows of a multiple of four floats on 16-byte boundaries (quaternions, SH rows):
+    // four elements of one row per thread and 16-byte accesses, one visibility test
+    // per vector; the same per-element update
+    const int w4 = width >> 2;
+    const int64_t total4 = n * w4;
+    float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m), *v4 = reinterpret_cast<float4 *>(v);
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total4; i += stride) {
+      if (radius && !visible(i / w4)) continue;
+      const float4 gi = g4[i];
+      float4 pi = p4[i], mi = m4[i], vi = v4[i];
+      update(pi.x, mi.x, vi.x, gi.x);
+      update(pi.y, mi.y, vi.y, gi.y);
+      update(pi.z, mi.z, vi.z, gi.z);
+      update(pi.w, mi.w, vi.w, gi.w);
+      m4[i] = mi;
+      v4[i] = vi;
+      p4[i] = pi;
     }
-    const float gi = g[i];
-    const float mi = beta1 * m[i] + (1.f - beta1) * gi;
-    const float vi = beta2 * v[i] + (1.f - beta2) * gi * gi;
+    return;
+  }
+  const int64_t total = n * width;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += stride) {
+    if (radius && !visible(i / width)) continue;
+    float pi = p[i], mi = m[i], vi = v[i];
+    update(pi, mi, vi, g[i]);
     m[i] = mi;
     v[i] = vi;
-    p[i] -= ss * mi / (sqrtf(vi) / sqrt_bc2 + eps);
+    p[i] = pi;
   }
 }
 
