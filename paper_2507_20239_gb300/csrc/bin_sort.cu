@@ -964,6 +964,9 @@ extern "C" gs_status_t gs_bin_sort(const gs_proj_t *proj, const gs_frame_t *fram
   //    (tile, record) pairs over the contiguous workspace words dk1 | dv1, which
   //    hold 8 * capacity bytes, and that pass reads them.
   const bool packed = passes == 1;
+  if (packed && reinterpret_cast<const char *>(w.dv1) - reinterpret_cast<const char *>(w.dk1) <
+                    (ptrdiff_t)(4 * (size_t)bins->capacity))
+    return GS_ERR_INVALID_ARG;   // the layout keeps dk1 | dv1 adjacent; never taken
   if (packed)
     bin_emit_kernel<true><<<eg, 256, 0, s>>>(order, n_vis, overflow, fbits, w.dhist, w.ubatch, ut0, uinf, B_k,
                                              nullptr, w.counters + 4, (uint64_t)bins->capacity);
