@@ -42,12 +42,14 @@ def test_fp32_peak_from_device_properties_and_clock(monkeypatch):
 
 def test_reference_arm_json_line():
     env = dict(os.environ)
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--n", "4000", "--cpu-sample-tiles", "4"],
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--n", "4000", "--cpu-sample-tiles", "4"],
                          capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "views/s" and line["value"] > 0
+    # the run the arguments ask for: K timed steps after W warm-ups
+    assert line["steps"] == 2 and line["warmup"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     # a step is one bounded sample: its wall time, and the fraction of a view it covers
     assert 0 < line["view_fraction_per_step"] <= 1
